@@ -1,0 +1,115 @@
+"""Shared test helpers: golden-fixture parsing and small brute-force checks."""
+from __future__ import annotations
+
+import glob
+import itertools
+import os
+
+import numpy as np
+
+from paper_2608_21826_gb300 import synth
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+INF = 2147483647
+
+
+def _ints(tokens):
+    return [INF if t == "INF" else int(t) for t in tokens]
+
+
+def load_golden(path):
+    """Parse one fixture into (Graph, expected dict)."""
+    lines = [ln.split("#")[0].strip() for ln in open(path)]
+    lines = [ln for ln in lines if ln]
+    V, src = map(int, lines[0].split())
+    assert lines[1] == "edges"
+    edges, exp = [], {}
+    for ln in lines[2:]:
+        tok = ln.split()
+        if tok[0] in ("dist", "hops", "status"):
+            exp[tok[0]] = _ints(tok[1:])
+        else:
+            edges.append(tuple(int(t) for t in tok))
+    u = np.array([e[0] for e in edges], np.int64)
+    v = np.array([e[1] for e in edges], np.int64)
+    w = np.array([e[2] for e in edges], np.int64)
+    row_ptr, col, order = synth.csr_from_edges(V, u, v, dedupe=False,
+                                               drop_self_loops=False, return_order=True)
+    g = synth.Graph(os.path.basename(path), row_ptr, col, w[order].astype(np.int32),
+                    np.array([src], np.int32))
+    exp["status"] = exp["status"][0]
+    return g, exp
+
+
+def golden_files():
+    return sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))
+
+
+def brute_force(g, src):
+    """Enumerate simple paths (tiny V only).  Returns (has_neg_cycle, dist, hops)
+    with dist/hops the lexicographic minimum over simple s->v paths and
+    has_neg_cycle true iff a simple cycle of negative weight is reachable."""
+    V = g.V
+    adj = {u: [] for u in range(V)}
+    for u in range(V):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            adj[u].append((int(g.col[e]), int(g.w[e])))
+    best = {src: (0, 0)}
+    reach = {src}
+
+    def dfs(u, d, h, on_path):
+        for v, w in adj[u]:
+            if v in on_path:
+                continue
+            nd, nh = d + w, h + 1
+            reach.add(v)
+            if v not in best or (nd, nh) < best[v]:
+                best[v] = (nd, nh)
+            on_path.add(v)
+            dfs(v, nd, nh, on_path)
+            on_path.discard(v)
+
+    dfs(src, 0, 0, {src})
+    neg = False
+    # simple cycles through each reachable start vertex c: DFS back to c
+    def cyc(c, u, d, on_path):
+        nonlocal neg
+        for v, w in adj[u]:
+            if v == c and d + w < 0:
+                neg = True
+            if v != c and v not in on_path and v > c:
+                on_path.add(v)
+                cyc(c, v, d + w, on_path)
+                on_path.discard(v)
+    for c in sorted(reach):
+        cyc(c, c, 0, {c})
+    dist = np.full(V, INF, np.int64)
+    hops = np.full(V, -1, np.int64)
+    for v, (d, h) in best.items():
+        dist[v], hops[v] = d, h
+    return neg, dist, hops
+
+
+def bfs_levels(g, src):
+    V = g.V
+    lev = np.full(V, -1, np.int64)
+    lev[src] = 0
+    front = [src]
+    while front:
+        nxt = []
+        for u in front:
+            for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+                v = int(g.col[e])
+                if lev[v] < 0:
+                    lev[v] = lev[u] + 1
+                    nxt.append(v)
+        front = nxt
+    return lev
+
+
+def shifted_expectation(dist_base, hops_base, p, s):
+    """d'(v) = d(v) + p(s) - p(v) for reachable v (potential transform)."""
+    p = p.astype(np.int64)
+    d = dist_base.astype(np.int64)
+    out = np.where(d == INF, INF, d + p[s] - p)
+    return out, hops_base

@@ -1,0 +1,122 @@
+"""Pins for the Broker Queue model (Algorithm 1): sequential runs equal the
+bounded-FIFO specification; seeded interleavings of many simulated threads
+conserve items and keep FIFO order by ticket position; the garbled slot
+release printed in READ_DATA stalls at the first wrap-around, which is why the
+model reads it as 2*(Pos//N + 1)."""
+import random
+
+import pytest
+
+from oracle import broker_queue as bq
+
+
+def _run_one(gen):
+    try:
+        while True:
+            assert next(gen) != "wait", "sequential run must never wait"
+    except StopIteration as stop:
+        return stop.value
+
+
+@pytest.mark.parametrize("bwd", [False, True])
+@pytest.mark.parametrize("seed", range(10))
+def test_sequential_equals_spec(seed, bwd):
+    rng = random.Random(seed)
+    N = rng.choice([1, 2, 3, 4, 8])
+    q = bq.BrokerQueueSim(N)
+    spec = bq.FifoSpec(N)
+    for step in range(300):
+        if rng.random() < 0.55:
+            x = rng.randrange(1000)
+            r, _ = _run_one(q.enqueue(x, bwd=bwd))
+            assert r == spec.enqueue(x)
+        else:
+            r, got = _run_one(q.dequeue(bwd=bwd))
+            rs, xs = spec.dequeue()
+            assert r == rs
+            if r == bq.OK:
+                assert got[0] == xs
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_interleaved_enqdeq_and_mixed(seed):
+    """Enqueues and dequeues run concurrently in a seeded random interleaving:
+    counters stay consistent, tickets form gap-free ranges and every dequeue
+    returns the item enqueued at its ticket position."""
+    rng = random.Random(seed)
+    N = rng.choice([2, 4, 8, 16])
+    q = bq.BrokerQueueSim(N)
+    n_enq = rng.randrange(1, 40)
+    n_deq = rng.randrange(1, 40)
+    ops = [("enq", 1000 + i, q.enqueue(1000 + i)) for i in range(n_enq)]
+    ops += [("deq", None, q.dequeue()) for _ in range(n_deq)]
+    rng.shuffle(ops)
+    res = bq.run_interleaved(q, [(k, g) for k, _, g in ops], seed)
+    enq_items, enq_pos, deq_items, deq_pos = [], [], [], []
+    for (kind, item, _), (status, val) in zip(ops, res):
+        if status != bq.OK:
+            continue
+        if kind == "enq":
+            enq_items.append(item)
+            enq_pos.append(val)
+        else:
+            deq_items.append(val[0])
+            deq_pos.append(val[1])
+    assert q.tail - q.head == len(enq_pos) - len(deq_pos)
+    assert q.count == q.tail - q.head
+    err = bq.check_fifo_positions(enq_items, enq_pos, deq_items, deq_pos)
+    assert err is None, err
+
+
+def test_interleaved_items_follow_positions():
+    """Enqueue distinct items concurrently, then dequeue concurrently: the item
+    at each dequeue position is the one enqueued at that position."""
+    for seed in range(8):
+        N = 8
+        q = bq.BrokerQueueSim(N)
+        items = list(range(500, 512))
+        enq_ops = [("enq", q.enqueue(x)) for x in items]
+        res = bq.run_interleaved(q, enq_ops, seed)
+        pos_of = {x: r[1] for x, r in zip(items, res) if r[0] == bq.OK}
+        assert len(pos_of) == N                  # capacity reached, rest FULL
+        assert sum(r[0] == bq.FULL for r in res) == len(items) - N
+        deq_ops = [("deq", q.dequeue()) for _ in range(12)]
+        dres = bq.run_interleaved(q, deq_ops, seed + 100)
+        got = [r[1] for r in dres if r[0] == bq.OK]
+        assert len(got) == N
+        err = bq.check_fifo_positions(list(pos_of), list(pos_of.values()),
+                                      [x for x, _ in got], [p for _, p in got])
+        assert err is None, err
+
+
+def test_printed_release_ticket_stalls_after_wrap():
+    """READ_DATA as printed releases the slot with 2*(Pos + N/N) = 2*(Pos+1);
+    the enqueuer of the next lap waits for 2*(Pos//N + 1).  The two agree only
+    for Pos = 0, so the second lap stalls on slot 1."""
+    N = 4
+    q = bq.BrokerQueueSim(N, release_ticket=lambda pos, n: 2 * (pos + n // n))
+    for x in range(N):
+        r, _ = bq.run_interleaved(q, [("e", q.enqueue(x))], 0)[0]
+        assert r == bq.OK
+    for _ in range(N):
+        r, _ = bq.run_interleaved(q, [("d", q.dequeue())], 0)[0]
+        assert r == bq.OK
+    # second lap: slot 1's ticket is 4, the enqueuer wants 2
+    with pytest.raises(RuntimeError, match="stalled"):
+        for x in range(N):
+            bq.run_interleaved(q, [("e", q.enqueue(x))], 0, max_steps=10_000)
+    # the model's reading completes many laps
+    q2 = bq.BrokerQueueSim(N)
+    for lap in range(5):
+        for x in range(N):
+            assert bq.run_interleaved(q2, [("e", q2.enqueue(x))], 0)[0][0] == bq.OK
+        for x in range(N):
+            r, (item, _) = bq.run_interleaved(q2, [("d", q2.dequeue())], 0)[0]
+            assert r == bq.OK and item == x
+
+
+def test_check_fifo_positions_rejects_mismatch():
+    assert bq.check_fifo_positions([1, 2], [0, 1], [2, 1], [1, 0]) is None
+    assert bq.check_fifo_positions([1, 2], [0, 1], [1, 2], [1, 0]) is not None
+    assert bq.check_fifo_positions([1, 2], [0, 2], [], []) is not None
+    assert bq.check_fifo_positions([1], [0], [1, 1], [0, 1]) is not None
