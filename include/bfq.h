@@ -1,0 +1,196 @@
+/*
+ * bfq.h -- C ABI of a single-GPU (GB300, sm_103a) queue-driven Bellman-Ford
+ * SSSP library.
+ *
+ * The method is the one of "A Concurrent Queue System for Multi-GPU Platforms:
+ * Application to Bellman-Ford SSSP": active vertices flow through a Broker
+ * Queue (Sec. III-A, Algorithm 1) -- a ring buffer with head/tail ticket
+ * counters, per-slot tickets and a broker count reserved before a ticket is
+ * taken -- and each dequeued vertex relaxes its out-edges (Sec. III-C,
+ * Algorithm 3).  The paper's per-GPU queue partitions (Sec. III-B,
+ * Algorithm 2) become per-CTA sub-queues with work stealing on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Return value: >= 0 is a status (BFQ_OK, BFQ_NEG_CYCLE, ...), < 0 an
+ *     error.  bfq_last_error() returns a message for the last error raised
+ *     by the calling host thread.
+ *   - "device pointer" arguments are caller-owned CUDA device memory (for
+ *     instance torch tensors); the library never frees them.  "host pointer"
+ *     arguments are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is enqueued on it; functions documented as synchronising
+ *     wait for it.
+ *   - A handle (graph, queue, batch, server) is not thread-safe: calls on one
+ *     handle must be serialised by the caller, and GPU work issued through one
+ *     handle on different streams must not overlap.
+ *   - Graph data: CSR with int32 row_ptr[V+1], col[E], w[E]; 0 <= col < V;
+ *     row_ptr non-decreasing from 0 to E.  Parallel edges and self-loops are
+ *     allowed.
+ *   - Distances are int32.  INT32_MAX (2147483647) means "no path".  A
+ *     candidate distance >= INT32_MAX is discarded; a candidate <= INT32_MIN
+ *     stops the run with status BFQ_RANGE.  hops[v] is the edge count of the
+ *     least (dist, hops) label (the least-weight path with the fewest edges),
+ *     -1 when unreachable.
+ *   - Negative cycles (Algorithm 3 reports "detection of negative cycles"):
+ *     status BFQ_NEG_CYCLE iff a negative-weight cycle is reachable from the
+ *     source; dist/hops/pred contents are then unspecified.  Detection is
+ *     exact: without such a cycle every accepted label is a simple path, so an
+ *     accepted label with hops >= V proves one.  If V * max(0, -min weight)
+ *     >= 2^31 and such a cycle exists, BFQ_RANGE may be returned instead.
+ *   - Every device-side wait is bounded; a run that exceeds its bounds ends
+ *     with BFQ_ERR_TIMEOUT and leaves the CUDA context usable.
+ */
+#ifndef BFQ_H
+#define BFQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status and error codes ------------------------------------------- */
+enum {
+  BFQ_OK = 0,            /* finished, results valid                         */
+  BFQ_NEG_CYCLE = 1,     /* a negative cycle is reachable from the source   */
+  BFQ_FULL = 2,          /* queue: enqueue refused, ring holds N items      */
+  BFQ_EMPTY = 3,         /* queue: dequeue refused, ring holds no item      */
+  BFQ_RANGE = 4,         /* a distance fell below the int32 range           */
+  BFQ_PENDING = 5,       /* server: request not finished yet                */
+  BFQ_ERR_INVALID = -1,  /* bad argument or malformed graph                 */
+  BFQ_ERR_OOM = -2,      /* device or host allocation failed                */
+  BFQ_ERR_TIMEOUT = -3,  /* a bounded device-side wait ran out              */
+  BFQ_ERR_CUDA = -4,     /* a CUDA call failed                              */
+  BFQ_ERR_BUDGET = -5    /* server: request can never fit the memory budget */
+};
+
+/* Queue variants (Sec. III-A). */
+enum {
+  BFQ_QUEUE_BQ = 0,      /* Broker Queue, one operation per thread (Alg. 1)  */
+  BFQ_QUEUE_BWD = 1,     /* Broker Work Distributor: ensure tried once        */
+  BFQ_QUEUE_BQ_WARP = 2  /* Broker Queue, warp-aggregated: one count/ticket
+                            reservation per warp, the form the SSSP path uses */
+};
+
+typedef struct bfq_graph* bfq_graph_t;
+typedef struct bfq_queue* bfq_queue_t;
+typedef struct bfq_batch* bfq_batch_t;
+typedef struct bfq_server* bfq_server_t;
+
+/* Launch and queue parameters of the persistent SSSP kernel.  Zero in any
+ * field selects the library default for it (bfq_tune_default). */
+typedef struct bfq_tune {
+  int32_t ctas_per_sm;      /* persistent CTAs per SM                        */
+  int32_t threads_per_cta;  /* multiple of 32, <= 1024                       */
+  int32_t queues_per_cta;   /* sub-queues per CTA (>= 1)                     */
+  int32_t batch_items;      /* max vertices a warp dequeues at once (<= 32)  */
+  int32_t hub_degree;       /* out-degree above which a vertex is split into
+                               edge chunks shared by many warps             */
+  int32_t chunk_edges;      /* edges per hub chunk (multiple of 32)          */
+  int64_t spin_limit;       /* max polls of one ticket slot                  */
+  int64_t time_limit_ms;    /* max wall time of one run on the device        */
+  int32_t l2_persist_pct;   /* 0..100: share of the L2 set-aside asked for the
+                               label array (access-policy window); 0 = off  */
+  int32_t test_phantom_items; /* test hook, 0 in normal use: in-flight items
+                               that no queued item backs, so a run can only
+                               end through time_limit_ms (BFQ_ERR_TIMEOUT) */
+  int32_t reserved[6];
+} bfq_tune;
+
+/* Counters of the last finished run on a graph handle (summed over warps). */
+typedef struct bfq_stats {
+  int64_t dequeued;       /* items taken from sub-queues (vertices + chunks)  */
+  int64_t relaxed;        /* edges scanned                                   */
+  int64_t updated;        /* successful label decreases                      */
+  int64_t enqueued;       /* vertices enqueued (bitmap test-and-set won)     */
+  int64_t steals;         /* dequeues from a sub-queue other than home       */
+  int64_t hub_chunks;     /* hub edge chunks processed                       */
+  int64_t m_reached;      /* edges whose tail is reachable (GTEPS numerator) */
+  int64_t reached;        /* reachable vertices                              */
+  int64_t V, E;
+  int32_t grid, block, queues, queue_capacity;
+  double kernel_ms;       /* duration of the persistent relaxation kernel,
+                             from CUDA events recorded around its launch on
+                             the caller's stream                            */
+  int64_t reserved[5];
+} bfq_stats;
+
+/* ---- errors ------------------------------------------------------------ */
+/* Message of the last error raised on this host thread ("" if none). */
+const char* bfq_last_error(void);
+/* Library ABI version (major*10000 + minor*100 + patch). */
+int32_t bfq_version(void);
+
+/* ---- tuning ------------------------------------------------------------- */
+/* Fill *t with the defaults for the current device.  Returns BFQ_OK. */
+int bfq_tune_default(bfq_tune* t);
+
+/* ---- graphs (graph residency, Sec. III-C: graph data moved to GPU memory) */
+/* Copy a CSR graph into library-owned device memory (interleaved
+ * (col, w) pairs, 8 B per edge) and allocate its per-run workspace (labels,
+ * in-queue bitmap, sub-queues).  row_ptr/col/w are host pointers when
+ * on_device == 0, device pointers otherwise (read on `stream`).  The graph
+ * is validated (monotone row_ptr, 0 <= col < V); BFQ_ERR_INVALID otherwise.
+ * Synchronises `stream`.  tune may be NULL (defaults). */
+int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E,
+                     const int32_t* row_ptr, const int32_t* col,
+                     const int32_t* w, int on_device, const bfq_tune* tune,
+                     void* stream);
+int bfq_graph_destroy(bfq_graph_t g);
+/* Device memory the handle holds, in bytes (graph + workspace). */
+int64_t bfq_graph_device_bytes(bfq_graph_t g);
+
+/* ---- single-source shortest paths (Algorithm 3 on one GPU) --------------- */
+/* One query from `src`.  dist (int32[V], device) receives distances; hops
+ * and pred (int32[V], device, each nullable) receive edge counts and a
+ * predecessor tree (pred[src] = -1, -1 when unreachable; any tight
+ * predecessor u with hops[u] + 1 == hops[v]).  Synchronises `stream` and
+ * returns BFQ_OK, BFQ_NEG_CYCLE, BFQ_RANGE or an error. */
+int bfq_sssp(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
+             int32_t* pred, void* stream);
+/* Same, without synchronising: the status code (int32) is written to
+ * status_dev (device pointer) when the run finishes on `stream`.  Returns
+ * BFQ_OK once the work is enqueued, or an argument error. */
+int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
+                   int32_t* pred, int32_t* status_dev, void* stream);
+/* Counters of the last run on g (synchronises the device). */
+int bfq_get_stats(bfq_graph_t g, bfq_stats* out);
+
+/* ---- standalone Broker Queue (Sec. III-A, Algorithm 1; Sec. IV workloads) */
+/* A ring of `capacity` int32 items (rounded up to a power of two for the
+ * warp variant), variant = BFQ_QUEUE_*. */
+int bfq_queue_create(bfq_queue_t* q, int64_t capacity, int32_t variant);
+int bfq_queue_destroy(bfq_queue_t q);
+/* Reset head, tail, count and tickets to zero (INITIALIZE). */
+int bfq_queue_reset(bfq_queue_t q, void* stream);
+/* n ENQUEUE operations of items[i] (device), op i by thread i of a
+ * grid-stride loop over grid x block threads.  pos_out (int64[n], device,
+ * nullable) receives the ring position (tail ticket) of each successful op
+ * or -1 for BFQ_FULL.  Asynchronous. */
+int bfq_queue_enqueue(bfq_queue_t q, const int32_t* items, int64_t n,
+                      int64_t* pos_out, int32_t grid, int32_t block,
+                      void* stream);
+/* n DEQUEUE operations; out[i] (device) receives the item of op i, pos_out
+ * (nullable) its head ticket or -1 for BFQ_EMPTY.  Asynchronous. */
+int bfq_queue_dequeue(bfq_queue_t q, int32_t* out, int64_t n,
+                      int64_t* pos_out, int32_t grid, int32_t block,
+                      void* stream);
+/* The paper's "Global Mixed" workload: in one launch, even blocks perform
+ * n_enq ENQUEUEs of items[] and odd blocks n_deq DEQUEUEs into out[];
+ * enq_pos/deq_pos as above (nullable).  grid >= 2.  Asynchronous. */
+int bfq_queue_mixed(bfq_queue_t q, const int32_t* items, int64_t n_enq,
+                    int64_t* enq_pos, int32_t* out, int64_t n_deq,
+                    int64_t* deq_pos, int32_t grid, int32_t block,
+                    void* stream);
+/* Read head, tail and count (host pointers, each nullable) and the queue's
+ * error word; synchronises `stream`.  Returns BFQ_OK or BFQ_ERR_TIMEOUT if a
+ * ticket wait of an earlier launch ran out. */
+int bfq_queue_state(bfq_queue_t q, int64_t* head, int64_t* tail,
+                    int64_t* count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFQ_H */

@@ -1,0 +1,273 @@
+"""Thin ctypes binding of libbfq (the C ABI declared in include/bfq.h).
+
+Each ``bfq_*`` function here marshals its arguments (numpy arrays, torch
+tensors, raw pointers, streams) and calls the C entry point of the same name;
+all computation runs in the library's CUDA kernels.  There is no fallback:
+if the library cannot be built or loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK, NEG_CYCLE, FULL, EMPTY, RANGE, PENDING = 0, 1, 2, 3, 4, 5
+ERR_INVALID, ERR_OOM, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = -1, -2, -3, -4, -5
+QUEUE_BQ, QUEUE_BWD, QUEUE_BQ_WARP = 0, 1, 2
+INF32 = 2147483647
+
+
+class BfqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bfq error {code}: {msg}")
+        self.code = code
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("queues_per_cta", ctypes.c_int32), ("batch_items", ctypes.c_int32),
+                ("hub_degree", ctypes.c_int32), ("chunk_edges", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("time_limit_ms", ctypes.c_int64),
+                ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("dequeued", ctypes.c_int64), ("relaxed", ctypes.c_int64),
+                ("updated", ctypes.c_int64), ("enqueued", ctypes.c_int64),
+                ("steals", ctypes.c_int64), ("hub_chunks", ctypes.c_int64),
+                ("m_reached", ctypes.c_int64), ("reached", ctypes.c_int64),
+                ("V", ctypes.c_int64), ("E", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("queues", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 5)]
+
+
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_SIGNATURES = {
+    "bfq_last_error": ([], ctypes.c_char_p),
+    "bfq_version": ([], _I32),
+    "bfq_tune_default": ([ctypes.POINTER(Tune)], ctypes.c_int),
+    "bfq_graph_create": ([ctypes.POINTER(_VP), _I32, _I64, _VP, _VP, _VP, ctypes.c_int,
+                          ctypes.POINTER(Tune), _VP], ctypes.c_int),
+    "bfq_graph_destroy": ([_VP], ctypes.c_int),
+    "bfq_graph_device_bytes": ([_VP], _I64),
+    "bfq_sssp": ([_VP, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "bfq_sssp_async": ([_VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "bfq_get_stats": ([_VP, ctypes.POINTER(Stats)], ctypes.c_int),
+    "bfq_queue_create": ([ctypes.POINTER(_VP), _I64, _I32], ctypes.c_int),
+    "bfq_queue_destroy": ([_VP], ctypes.c_int),
+    "bfq_queue_reset": ([_VP, _VP], ctypes.c_int),
+    "bfq_queue_enqueue": ([_VP, _VP, _I64, _VP, _I32, _I32, _VP], ctypes.c_int),
+    "bfq_queue_dequeue": ([_VP, _VP, _I64, _VP, _I32, _I32, _VP], ctypes.c_int),
+    "bfq_queue_mixed": ([_VP, _VP, _I64, _VP, _VP, _I64, _VP, _I32, _I32, _VP], ctypes.c_int),
+    "bfq_queue_state": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                         ctypes.POINTER(_I64), _VP], ctypes.c_int),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbfq.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            handle = ctypes.CDLL(path)
+            for name, (args, res) in _SIGNATURES.items():
+                f = getattr(handle, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = handle
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def last_error() -> str:
+    return lib().bfq_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise BfqError(rc, last_error())
+    return rc
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, int address or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return _VP(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return _VP(x.ctypes.data)
+    if isinstance(x, int):
+        return _VP(x)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    """cudaStream_t from a torch stream, an int handle, or the current torch
+    stream when None."""
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return _VP(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(s, "cuda_stream"):
+        return _VP(s.cuda_stream)
+    return _VP(int(s))
+
+
+def _is_device(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def tune_default() -> Tune:
+    t = Tune()
+    _check(lib().bfq_tune_default(ctypes.byref(t)))
+    return t
+
+
+def make_tune(**kw) -> Tune:
+    t = tune_default()
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+# ---- graphs -----------------------------------------------------------------
+
+def bfq_graph_create(row_ptr, col, w, tune: Tune | None = None, stream=None):
+    """CSR arrays as host numpy int32 arrays or CUDA int32 tensors."""
+    on_dev = _is_device(row_ptr)
+    if on_dev != _is_device(col) or on_dev != _is_device(w):
+        raise ValueError("row_ptr, col and w must all be host or all be device arrays")
+    if not on_dev:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+    V = len(row_ptr) - 1
+    E = len(col)
+    h = _VP()
+    _check(lib().bfq_graph_create(ctypes.byref(h), V, E, _ptr(row_ptr), _ptr(col), _ptr(w),
+                                  int(on_dev), ctypes.byref(tune) if tune else None,
+                                  _stream(stream)))
+    return h
+
+
+def bfq_graph_destroy(g) -> None:
+    _check(lib().bfq_graph_destroy(g))
+
+
+def bfq_graph_device_bytes(g) -> int:
+    return int(lib().bfq_graph_device_bytes(g))
+
+
+def bfq_sssp(g, src: int, dist, hops=None, pred=None, stream=None) -> int:
+    """Synchronous single-source query; returns OK / NEG_CYCLE / RANGE."""
+    return _check(lib().bfq_sssp(g, int(src), _ptr(dist), _ptr(hops), _ptr(pred),
+                                 _stream(stream)))
+
+
+def bfq_sssp_async(g, src: int, dist, hops=None, pred=None, status_dev=None, stream=None) -> int:
+    return _check(lib().bfq_sssp_async(g, int(src), _ptr(dist), _ptr(hops), _ptr(pred),
+                                       _ptr(status_dev), _stream(stream)))
+
+
+def bfq_get_stats(g) -> dict:
+    s = Stats()
+    _check(lib().bfq_get_stats(g, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+
+
+# ---- standalone queue ----------------------------------------------------------
+
+def bfq_queue_create(capacity: int, variant: int = QUEUE_BQ):
+    h = _VP()
+    _check(lib().bfq_queue_create(ctypes.byref(h), int(capacity), int(variant)))
+    return h
+
+
+def bfq_queue_destroy(q) -> None:
+    _check(lib().bfq_queue_destroy(q))
+
+
+def bfq_queue_reset(q, stream=None) -> None:
+    _check(lib().bfq_queue_reset(q, _stream(stream)))
+
+
+def bfq_queue_enqueue(q, items, pos_out=None, grid: int = 108, block: int = 256,
+                      stream=None) -> None:
+    _check(lib().bfq_queue_enqueue(q, _ptr(items), len(items), _ptr(pos_out), grid, block,
+                                   _stream(stream)))
+
+
+def bfq_queue_dequeue(q, out, pos_out=None, grid: int = 108, block: int = 256,
+                      stream=None) -> None:
+    _check(lib().bfq_queue_dequeue(q, _ptr(out), len(out), _ptr(pos_out), grid, block,
+                                   _stream(stream)))
+
+
+def bfq_queue_mixed(q, items, out, enq_pos=None, deq_pos=None, grid: int = 108,
+                    block: int = 256, stream=None) -> None:
+    _check(lib().bfq_queue_mixed(q, _ptr(items), len(items), _ptr(enq_pos), _ptr(out),
+                                 len(out), _ptr(deq_pos), grid, block, _stream(stream)))
+
+
+def bfq_queue_state(q, stream=None):
+    """(status, head, tail, count); status ERR_TIMEOUT if a wait ran out."""
+    h, t, c = _I64(), _I64(), _I64()
+    rc = lib().bfq_queue_state(q, ctypes.byref(h), ctypes.byref(t), ctypes.byref(c),
+                               _stream(stream))
+    return rc, h.value, t.value, c.value
+
+
+# ---- convenience object -----------------------------------------------------------
+
+class Graph:
+    """A resident graph: ``Graph(row_ptr, col, w).sssp(src)``."""
+
+    def __init__(self, row_ptr, col, w, tune: Tune | None = None, stream=None):
+        self.V = len(row_ptr) - 1
+        self.E = len(col)
+        self.handle = bfq_graph_create(row_ptr, col, w, tune, stream)
+
+    def sssp(self, src: int, dist=None, hops=None, pred=None, stream=None):
+        """Returns (status, dist, hops, pred) with CUDA int32 tensors."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty(self.V, dtype=torch.int32, device=dev)
+        st = bfq_sssp(self.handle, src, dist, hops, pred, stream)
+        return st, dist, hops, pred
+
+    def stats(self) -> dict:
+        return bfq_get_stats(self.handle)
+
+    def device_bytes(self) -> int:
+        return bfq_graph_device_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            bfq_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,82 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bfq.h"
+#include "bfq_device.cuh"
+
+namespace bfq {
+
+// Per-run control block in device memory; each hot field on its own line.
+struct alignas(128) Control {
+  int inflight;                 // items enqueued and not yet fully processed
+  int pad0[31];
+  int status;                   // kSt* bits of the current run
+  int pad1[31];
+  int stop;                     // set once a run must end early
+  int pad2[31];
+  unsigned long long ctr[8];    // summed warp counters, see CtrIndex
+  unsigned long long pad3[8];
+  int last_status;              // status code of the previous run (0 = clean)
+  int pad4[31];
+};
+
+enum CtrIndex { kCtrDeq = 0, kCtrRel, kCtrUpd, kCtrEnq, kCtrSteal, kCtrChunk, kCtrIdle, kCtrSpare };
+
+struct SsspArgs {
+  const int* row_ptr;           // [V+1]
+  const int2* adj;              // [E] (col, w)
+  long long* label;             // [V] packed (dist, hops)
+  unsigned* bitmap;             // [ceil(V/32)] in-queue bits
+  QueueSet qs;                  // vertex sub-queues
+  QueueSet cq;                  // hub edge-chunk sub-queues
+  const int* hub_chunk0;        // [V] first chunk-table entry of a hub (read for hubs only)
+  const int4* chunk_tab;        // {u, beg, end, 0} per hub chunk
+  Control* ctl;
+  int* dist;                    // [V] output
+  int* hops;                    // [V] output or null
+  int* pred;                    // [V] output or null (initialised to -1 here)
+  int V;
+  int src;
+  int batch_items;
+  int queues_per_cta;
+  int hub_degree;
+  int chunk_edges;
+  long long spin_limit;
+  long long time_limit_ns;
+  int phantom;                  // test hook: unbacked in-flight items
+};
+
+struct LaunchShape {
+  int grid;
+  int block;
+};
+
+// Thread-local last-error message (bfq_last_error).
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define BFQ_CUDA_TRY(call)                                                     \
+  do {                                                                         \
+    cudaError_t e__ = (call);                                                  \
+    if (e__ != cudaSuccess) return ::bfq::cuda_fail(e__, #call, __FILE__, __LINE__); \
+  } while (0)
+
+// Kernels launchers (sssp.cu)
+int sssp_max_ctas_per_sm(int block);
+// init, persistent run (bracketed by ev0/ev1 when given), finalize, pred.
+cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,
+                        int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
+                        cudaStream_t s);
+cudaError_t launch_reached_edges(const int* row_ptr, const long long* label, int V,
+                                 unsigned long long* out2, cudaStream_t s);
+cudaError_t launch_pack_adj(const int* col, const int* w, int2* adj, long long E, cudaStream_t s);
+cudaError_t launch_validate_csr(const int* row_ptr, const int* col, int V, long long E,
+                                int* bad, cudaStream_t s);
+cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s);
+
+}  // namespace bfq

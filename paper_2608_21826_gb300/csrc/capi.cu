@@ -1,0 +1,362 @@
+// C ABI: graph residency, single-query SSSP, statistics and errors.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bfq_internal.h"
+
+namespace bfq {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file,
+                line);
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? BFQ_ERR_OOM : BFQ_ERR_CUDA;
+}
+
+static int invalid(const std::string& msg) {
+  set_error(msg);
+  return BFQ_ERR_INVALID;
+}
+
+static int ceil_log2(long long x) {
+  int l = 0;
+  while ((1LL << l) < x) ++l;
+  return l;
+}
+
+}  // namespace bfq
+
+using namespace bfq;
+
+struct bfq_graph {
+  int device = 0;
+  int V = 0;
+  long long E = 0;
+  bfq_tune tune{};
+  int* row_ptr = nullptr;
+  int2* adj = nullptr;
+  long long* label = nullptr;
+  unsigned* bitmap = nullptr;
+  QueueSet qs{};
+  QueueSet cq{};
+  int* hub_chunk0 = nullptr;
+  int4* chunk_tab = nullptr;
+  int n_chunks = 0;
+  Control* ctl = nullptr;
+  int32_t* status_dev = nullptr;
+  unsigned long long* scratch = nullptr;   // [2] reached-edge reduction
+  int32_t* status_host = nullptr;          // pinned
+  LaunchShape init_shape{};
+  LaunchShape run_shape{};
+  long long bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the persistent kernel
+  std::vector<void*> allocs;
+
+  int alloc(void** p, size_t n) {
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+    allocs.push_back(*p);
+    bytes += (long long)n;
+    return BFQ_OK;
+  }
+  ~bfq_graph() {
+    for (void* p : allocs) cudaFree(p);
+    if (status_host) cudaFreeHost(status_host);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+extern "C" {
+
+const char* bfq_last_error(void) { return g_last_error.c_str(); }
+
+int32_t bfq_version(void) { return 10000; }
+
+int bfq_tune_default(bfq_tune* t) {
+  if (!t) return invalid("bfq_tune_default: null pointer");
+  std::memset(t, 0, sizeof(*t));
+  t->threads_per_cta = 256;
+  t->ctas_per_sm = 0;          // 0: as many as fit (occupancy)
+  t->queues_per_cta = 1;
+  t->batch_items = 32;
+  t->hub_degree = 512;
+  t->chunk_edges = 256;
+  t->spin_limit = 1LL << 22;
+  t->time_limit_ms = 20000;
+  t->l2_persist_pct = 0;
+  return BFQ_OK;
+}
+
+static int fill_tune(const bfq_tune* in, bfq_tune* out) {
+  bfq_tune_default(out);
+  if (!in) return BFQ_OK;
+  if (in->threads_per_cta) out->threads_per_cta = in->threads_per_cta;
+  if (in->ctas_per_sm) out->ctas_per_sm = in->ctas_per_sm;
+  if (in->queues_per_cta) out->queues_per_cta = in->queues_per_cta;
+  if (in->batch_items) out->batch_items = in->batch_items;
+  if (in->hub_degree) out->hub_degree = in->hub_degree;
+  if (in->chunk_edges) out->chunk_edges = in->chunk_edges;
+  if (in->spin_limit) out->spin_limit = in->spin_limit;
+  if (in->time_limit_ms) out->time_limit_ms = in->time_limit_ms;
+  if (in->l2_persist_pct) out->l2_persist_pct = in->l2_persist_pct;
+  out->test_phantom_items = in->test_phantom_items;
+  if (out->threads_per_cta != 256)
+    return invalid("bfq_tune: threads_per_cta must be 256 in this build");
+  if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
+    return invalid("bfq_tune: queues_per_cta must be in [1, 8]");
+  if (out->batch_items < 1 || out->batch_items > 32)
+    return invalid("bfq_tune: batch_items must be in [1, 32]");
+  if (out->chunk_edges < 32 || out->chunk_edges % 32)
+    return invalid("bfq_tune: chunk_edges must be a positive multiple of 32");
+  if (out->hub_degree < out->chunk_edges)
+    return invalid("bfq_tune: hub_degree must be >= chunk_edges");
+  if (out->spin_limit < 1 || out->time_limit_ms < 1 || out->ctas_per_sm < 0 ||
+      out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0)
+    return invalid("bfq_tune: bad limits");
+  return BFQ_OK;
+}
+
+int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_ptr,
+                     const int32_t* col, const int32_t* w, int on_device, const bfq_tune* tune,
+                     void* stream) {
+  if (!out) return invalid("bfq_graph_create: out is null");
+  *out = nullptr;
+  if (V < 1) return invalid("bfq_graph_create: V must be >= 1");
+  if (E < 0 || E >= (1LL << 31)) return invalid("bfq_graph_create: E must be in [0, 2^31)");
+  if (!row_ptr || (E > 0 && (!col || !w))) return invalid("bfq_graph_create: null CSR array");
+  cudaStream_t s = (cudaStream_t)stream;
+  bfq_graph* g = new (std::nothrow) bfq_graph();
+  if (!g) return invalid("bfq_graph_create: host allocation failed");
+  int rc = fill_tune(tune, &g->tune);
+  if (rc) { delete g; return rc; }
+  g->V = V;
+  g->E = E;
+  cudaGetDevice(&g->device);
+
+  // host copy of row_ptr (validation on the host when the CSR is host-side,
+  // hub chunk table in both cases)
+  std::vector<int> rp(V + 1);
+#define G_TRY(x)                                        \
+  do {                                                  \
+    int rc__ = (x);                                     \
+    if (rc__ != BFQ_OK) { delete g; return rc__; }      \
+  } while (0)
+#define G_CUDA(x)                                                              \
+  do {                                                                         \
+    cudaError_t e__ = (x);                                                     \
+    if (e__ != cudaSuccess) { int rc__ = cuda_fail(e__, #x, __FILE__, __LINE__); delete g; return rc__; } \
+  } while (0)
+  if (on_device) {
+    G_CUDA(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int) * (V + 1), cudaMemcpyDeviceToHost, s));
+    G_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(rp.data(), row_ptr, sizeof(int) * (V + 1));
+  }
+  if (rp[0] != 0 || (long long)rp[V] != E) { delete g; return invalid("bfq_graph_create: row_ptr[0] must be 0 and row_ptr[V] == E"); }
+  for (int v = 0; v < V; ++v)
+    if (rp[v + 1] < rp[v]) { delete g; return invalid("bfq_graph_create: row_ptr not monotone"); }
+  if (!on_device) {
+    for (long long i = 0; i < E; ++i)
+      if (col[i] < 0 || col[i] >= V) { delete g; return invalid("bfq_graph_create: col out of range"); }
+  }
+
+  // graph arrays
+  G_TRY(g->alloc((void**)&g->row_ptr, sizeof(int) * (V + 1)));
+  G_TRY(g->alloc((void**)&g->adj, sizeof(int2) * (size_t)E));
+  G_CUDA(cudaMemcpyAsync(g->row_ptr, rp.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, s));
+  if (E > 0) {
+    if (on_device) {
+      int* bad = nullptr;
+      G_CUDA(cudaMalloc((void**)&bad, sizeof(int)));
+      cudaError_t e1 = cudaMemsetAsync(bad, 0, sizeof(int), s);
+      if (e1 == cudaSuccess) e1 = launch_validate_csr(g->row_ptr, col, V, E, bad, s);
+      if (e1 == cudaSuccess) e1 = launch_pack_adj(col, w, g->adj, E, s);
+      int hbad = 0;
+      if (e1 == cudaSuccess) e1 = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s);
+      cudaFree(bad);
+      G_CUDA(e1);
+      if (hbad) { delete g; return invalid("bfq_graph_create: col out of range"); }
+    } else {
+      std::vector<int2> packed((size_t)E);
+      for (long long i = 0; i < E; ++i) packed[i] = make_int2(col[i], w[i]);
+      G_CUDA(cudaMemcpyAsync(g->adj, packed.data(), sizeof(int2) * (size_t)E,
+                             cudaMemcpyHostToDevice, s));
+      G_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+
+  // hub chunk table: vertices of degree > hub_degree, chunk_edges per chunk
+  const int hub = g->tune.hub_degree, ce = g->tune.chunk_edges;
+  std::vector<int> chunk0(V, -1);
+  std::vector<int4> tab;
+  for (int v = 0; v < V; ++v) {
+    const int d = rp[v + 1] - rp[v];
+    if (d > hub) {
+      chunk0[v] = (int)tab.size();
+      for (int b = rp[v]; b < rp[v + 1]; b += ce)
+        tab.push_back(make_int4(v, b, std::min(b + ce, rp[v + 1]), 0));
+    }
+  }
+  g->n_chunks = (int)tab.size();
+  G_TRY(g->alloc((void**)&g->hub_chunk0, sizeof(int) * V));
+  G_TRY(g->alloc((void**)&g->chunk_tab, sizeof(int4) * std::max<size_t>(1, tab.size())));
+  G_CUDA(cudaMemcpyAsync(g->hub_chunk0, chunk0.data(), sizeof(int) * V, cudaMemcpyHostToDevice, s));
+  if (!tab.empty())
+    G_CUDA(cudaMemcpyAsync(g->chunk_tab, tab.data(), sizeof(int4) * tab.size(),
+                           cudaMemcpyHostToDevice, s));
+
+  // launch shape
+  int sms = 0;
+  G_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+  const int block = g->tune.threads_per_cta;
+  int per_sm = sssp_max_ctas_per_sm(block);
+  if (g->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, g->tune.ctas_per_sm);
+  g->run_shape = {sms * per_sm, block};
+  g->init_shape = {sms * 4, 256};
+
+  // workspace: labels, in-queue bitmap, vertex and chunk sub-queues
+  const int Q = g->run_shape.grid * g->tune.queues_per_cta;
+  const long long per_q = (2LL * V + Q - 1) / Q;
+  int cap_log2 = std::max(10, ceil_log2(per_q));
+  g->qs.Q = Q;
+  g->qs.cap_log2 = cap_log2;
+  const int Qc = g->n_chunks > 0 ? g->run_shape.grid : 1;
+  const long long per_qc = (4LL * g->n_chunks + Qc - 1) / Qc;
+  g->cq.Q = Qc;
+  g->cq.cap_log2 = std::max(8, ceil_log2(std::max(1LL, per_qc)));
+  const long long words = ((long long)V + 31) / 32;
+  G_TRY(g->alloc((void**)&g->label, sizeof(long long) * (size_t)V));
+  G_TRY(g->alloc((void**)&g->bitmap, sizeof(unsigned) * (size_t)words));
+  G_TRY(g->alloc((void**)&g->qs.meta, sizeof(QueueMeta) * Q));
+  G_TRY(g->alloc((void**)&g->qs.slots, sizeof(unsigned long long) * ((size_t)Q << cap_log2)));
+  G_TRY(g->alloc((void**)&g->cq.meta, sizeof(QueueMeta) * Qc));
+  G_TRY(g->alloc((void**)&g->cq.slots,
+                 sizeof(unsigned long long) * ((size_t)Qc << g->cq.cap_log2)));
+  G_TRY(g->alloc((void**)&g->ctl, sizeof(Control)));
+  G_TRY(g->alloc((void**)&g->status_dev, sizeof(int32_t)));
+  G_TRY(g->alloc((void**)&g->scratch, 2 * sizeof(unsigned long long)));
+  G_CUDA(cudaMemsetAsync(g->bitmap, 0, sizeof(unsigned) * (size_t)words, s));
+  G_CUDA(cudaMemsetAsync(g->qs.meta, 0, sizeof(QueueMeta) * Q, s));
+  G_CUDA(cudaMemsetAsync(g->qs.slots, 0, sizeof(unsigned long long) * ((size_t)Q << cap_log2), s));
+  G_CUDA(cudaMemsetAsync(g->cq.meta, 0, sizeof(QueueMeta) * Qc, s));
+  G_CUDA(cudaMemsetAsync(g->cq.slots, 0,
+                         sizeof(unsigned long long) * ((size_t)Qc << g->cq.cap_log2), s));
+  G_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(Control), s));
+  G_CUDA(cudaMallocHost((void**)&g->status_host, sizeof(int32_t)));
+  G_CUDA(cudaEventCreate(&g->ev0));
+  G_CUDA(cudaEventCreate(&g->ev1));
+  G_CUDA(cudaStreamSynchronize(s));
+#undef G_TRY
+#undef G_CUDA
+  *out = g;
+  return BFQ_OK;
+}
+
+int bfq_graph_destroy(bfq_graph_t g) {
+  if (!g) return invalid("bfq_graph_destroy: null handle");
+  cudaDeviceSynchronize();
+  delete g;
+  return BFQ_OK;
+}
+
+int64_t bfq_graph_device_bytes(bfq_graph_t g) { return g ? g->bytes : 0; }
+
+static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
+                          int32_t* pred) {
+  SsspArgs a{};
+  a.row_ptr = g->row_ptr;
+  a.adj = g->adj;
+  a.label = g->label;
+  a.bitmap = g->bitmap;
+  a.qs = g->qs;
+  a.cq = g->cq;
+  a.hub_chunk0 = g->hub_chunk0;
+  a.chunk_tab = g->chunk_tab;
+  a.ctl = g->ctl;
+  a.dist = dist;
+  a.hops = hops;
+  a.pred = pred;
+  a.V = g->V;
+  a.src = src;
+  a.batch_items = g->tune.batch_items;
+  a.queues_per_cta = g->tune.queues_per_cta;
+  a.hub_degree = g->tune.hub_degree;
+  a.chunk_edges = g->tune.chunk_edges;
+  a.spin_limit = g->tune.spin_limit;
+  a.time_limit_ns = g->tune.time_limit_ms * 1000000LL;
+  a.phantom = g->tune.test_phantom_items;
+  return a;
+}
+
+int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* pred,
+                   int32_t* status_dev, void* stream) {
+  if (!g) return invalid("bfq_sssp: null graph handle");
+  if (src < 0 || src >= g->V) return invalid("bfq_sssp: source out of range");
+  if (!dist) return invalid("bfq_sssp: dist is null");
+  cudaStream_t s = (cudaStream_t)stream;
+  g->last_stream = s;
+  SsspArgs a = make_args(g, src, dist, hops, pred);
+  BFQ_CUDA_TRY(launch_sssp(a, g->init_shape, g->run_shape, status_dev, g->ev0, g->ev1, s));
+  return BFQ_OK;
+}
+
+int bfq_sssp(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* pred,
+             void* stream) {
+  int rc = bfq_sssp_async(g, src, dist, hops, pred, g ? g->status_dev : nullptr, stream);
+  if (rc != BFQ_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  BFQ_CUDA_TRY(cudaMemcpyAsync(g->status_host, g->status_dev, sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, s));
+  BFQ_CUDA_TRY(cudaStreamSynchronize(s));
+  const int st = *g->status_host;
+  if (st == BFQ_ERR_TIMEOUT) set_error("bfq_sssp: a bounded device-side wait ran out");
+  return st;
+}
+
+int bfq_get_stats(bfq_graph_t g, bfq_stats* out) {
+  if (!g || !out) return invalid("bfq_get_stats: null argument");
+  std::memset(out, 0, sizeof(*out));
+  cudaStream_t s = g->last_stream;
+  BFQ_CUDA_TRY(cudaStreamSynchronize(s));
+  Control c;
+  BFQ_CUDA_TRY(cudaMemcpy(&c, g->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+  BFQ_CUDA_TRY(launch_reached_edges(g->row_ptr, g->label, g->V, g->scratch, s));
+  unsigned long long red[2] = {0, 0};
+  BFQ_CUDA_TRY(cudaMemcpyAsync(red, g->scratch, sizeof(red), cudaMemcpyDeviceToHost, s));
+  BFQ_CUDA_TRY(cudaStreamSynchronize(s));
+  out->dequeued = (int64_t)c.ctr[kCtrDeq];
+  out->relaxed = (int64_t)c.ctr[kCtrRel];
+  out->updated = (int64_t)c.ctr[kCtrUpd];
+  out->enqueued = (int64_t)c.ctr[kCtrEnq];
+  out->steals = (int64_t)c.ctr[kCtrSteal];
+  out->hub_chunks = (int64_t)c.ctr[kCtrChunk];
+  out->m_reached = (int64_t)red[0];
+  out->reached = (int64_t)red[1];
+  out->V = g->V;
+  out->E = g->E;
+  out->grid = g->run_shape.grid;
+  out->block = g->run_shape.block;
+  out->queues = g->qs.Q;
+  out->queue_capacity = 1 << g->qs.cap_log2;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
+  cudaGetLastError();   // no run yet: events never recorded
+  return BFQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,541 @@
+// Queue-driven Bellman-Ford SSSP on one GPU (Sec. III-C, Algorithm 3).
+//
+// One persistent kernel runs the whole query.  Every warp loops:
+//   dequeue a batch of up to 32 items (warp-aggregated Broker Queue,
+//   own sub-queue first, then stealing), relax their out-edges as one merged,
+//   lane-contiguous edge stream, enqueue the vertices whose label dropped and
+//   whose in-queue bit it won, and retire the batch from the in-flight count.
+// The run ends when the in-flight count reaches zero (this replaces the
+// paper's per-round change count and cross-GPU reduction), when a label with
+// hops >= V is accepted (negative cycle), or on a range error or timeout.
+//
+// Labels are (dist, hops) packed in 64 bits and lowered with atomicMin; the
+// relaxation test is the one of PARALLEL_RELAX_EDGES (Algorithm 3) applied to
+// the lexicographic label and made atomic (the listing's fetch / compare /
+// put sequence would lose concurrent updates).
+//
+// Vertices of out-degree > hub_degree are split into chunks of chunk_edges
+// edges published to a second set of sub-queues, so many warps share a hub.
+#include "bfq_internal.h"
+
+namespace bfq {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ void raise_status(Control* ctl, int bits) {
+  atomicOr(&ctl->status, bits);
+  st_relaxed_s32(&ctl->stop, 1);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
+  return x;
+}
+
+// Exclusive prefix of `x` over the warp; *total receives the sum.
+__device__ __forceinline__ int warp_excl_scan(int x, int lane, int* total) {
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int n = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += n;
+  }
+  *total = __shfl_sync(kFullMask, incl, 31);
+  return incl - x;
+}
+
+// For position t of a merged list, the owning lane: the largest j < n with
+// excl_j <= t (excl non-decreasing over lanes).
+__device__ __forceinline__ int owner_lane(int excl, int t, int n) {
+  int j = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int cand = j + step;
+    const int ex = __shfl_sync(kFullMask, excl, cand & 31);
+    if (cand < n && ex <= t) j = cand;
+  }
+  return j;
+}
+
+// Lanes probe up to 64 sub-queues starting at `start`; returns the fullest
+// non-empty one seen, or -1.
+__device__ __forceinline__ int probe_queues(const QueueSet& qs, int start, int skip, int lane) {
+  for (int r = 0; r < 2 && r * 32 < qs.Q; ++r) {
+    const int i = r * 32 + lane;
+    const int q = (start + i) % qs.Q;
+    const int c = (i < qs.Q && q != skip) ? ld_relaxed_s32(&qs.meta[q].count) : 0;
+    const int m = __reduce_max_sync(kFullMask, c);
+    if (m > 0) {
+      const unsigned who = __ballot_sync(kFullMask, c == m);
+      return __shfl_sync(kFullMask, q, __ffs(who) - 1);
+    }
+  }
+  return -1;
+}
+
+// Warp-collective enqueue of the lanes with `active` into the sub-queues of
+// qs, starting at `home` and moving on while a sub-queue is full, for at most
+// max_tries reservations.  Returns the number of items placed (the active
+// lanes of lowest rank), or -1 if a ticket wait ran out.
+__device__ __forceinline__ int enqueue_warp(const QueueSet& qs, int home, bool active,
+                                            unsigned item, int lane, long long spin_limit,
+                                            long long max_tries) {
+  const unsigned mask = __ballot_sync(kFullMask, active);
+  if (!mask) return 0;
+  const int k = __popc(mask);
+  const int rank = __popc(mask & ((1u << lane) - 1u));
+  const int cap = 1 << qs.cap_log2;
+  int done = 0;
+  int q = home;
+  for (long long tries = 0; done < k && tries < max_tries; ++tries) {
+    unsigned long long pos = 0;
+    int got = 0;
+    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos);
+    got = __shfl_sync(kFullMask, got, 0);
+    if (got) {
+      pos = __shfl_sync(kFullMask, pos, 0);
+      const int r = rank - done;
+      bool ok = true;
+      if (active && r >= 0 && r < got)
+        ok = wq_put(qs.slots + ((size_t)q << qs.cap_log2), qs.cap_log2, pos + r, item,
+                    spin_limit);
+      if (__any_sync(kFullMask, !ok)) return -1;
+      done += got;
+    }
+    q = (q + 1 == qs.Q) ? 0 : q + 1;
+  }
+  return done;
+}
+
+struct WarpCounters {
+  unsigned long long deq = 0, rel = 0, upd = 0, enq = 0, steal = 0, chunk = 0, idle = 0;
+};
+
+// Relax the merged edge lists of the items held by lanes [0, n): lane j owns
+// edges [beg_j, beg_j + deg_j) of a tail whose label is lab_j.  Edges are
+// walked lane-contiguously, 32 per step.  Returns false on a timeout.
+__device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
+                                             long long lab, int lane, int home,
+                                             WarpCounters& wc) {
+  int total = 0;
+  const int excl = warp_excl_scan(deg, lane, &total);
+  wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
+  const unsigned V = (unsigned)a.V;
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    const int j = owner_lane(excl, t, n);
+    const int ex_j = __shfl_sync(kFullMask, excl, j);
+    const int beg_j = __shfl_sync(kFullMask, beg, j);
+    const long long lab_j = __shfl_sync(kFullMask, lab, j);
+    bool want_enq = false;
+    unsigned v = 0;
+    if (t < total) {
+      const int2 cw = __ldg(&a.adj[beg_j + (t - ex_j)]);
+      v = (unsigned)cw.x;
+      const long long nd = (long long)label_dist(lab_j) + (long long)cw.y;
+      if (nd < (long long)kInf32) {
+        if (nd <= -2147483648LL) {
+          raise_status(a.ctl, kStRange);
+        } else {
+          const unsigned nh = label_hops(lab_j) + 1u;
+          const long long key = pack_label((int)nd, nh);
+          if (key < ld_relaxed_s64(&a.label[v])) {
+            const long long old = atomicMin((long long*)&a.label[v], key);
+            if (key < old) {
+              ++wc.upd;
+              if (nh >= V) {
+                raise_status(a.ctl, kStNegCycle);
+              } else {
+                // label write -> fence -> in-queue bit; pairs with the
+                // consumer's bit clear -> fence -> label read
+                fence_acq_rel_gpu();
+                const unsigned bit = 1u << (v & 31u);
+                const unsigned ob = atomicOr(&a.bitmap[v >> 5], bit);
+                want_enq = (ob & bit) == 0u;
+              }
+            }
+          }
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(kFullMask, want_enq);
+    if (m) {
+      // the new items are counted before any of them becomes visible
+      if (lane == 0) {
+        atomicAdd(&a.ctl->inflight, __popc(m));
+        wc.enq += __popc(m);
+      }
+      __syncwarp();
+      const int placed = enqueue_warp(a.qs, home, want_enq, v, lane, a.spin_limit,
+                                      4LL * a.qs.Q + 64);
+      if (placed != __popc(m)) {
+        if (lane == 0 && placed >= 0) atomicOr(&a.ctl->status, kStQueue);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// Publish the hub chunks [c0_j, c0_j + nch_j) of the lanes with nch > 0 to
+// the chunk sub-queues.  Chunks that find no room are relaxed right here.
+__device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
+                                            int home, int chome, WarpCounters& wc) {
+  int K = 0;
+  const int excl = warp_excl_scan(nch, lane, &K);
+  if (K == 0) return true;
+  if (lane == 0) atomicAdd(&a.ctl->inflight, K);
+  __syncwarp();
+  for (int base = 0; base < K; base += 32) {
+    const int t = base + lane;
+    const int j = owner_lane(excl, t, 32);
+    const int ex_j = __shfl_sync(kFullMask, excl, j);
+    const int c0_j = __shfl_sync(kFullMask, c0, j);
+    const bool act = t < K;
+    const unsigned id = (unsigned)(c0_j + (t - ex_j));
+    const int placed = enqueue_warp(a.cq, chome, act, id, lane, a.spin_limit, 2LL * a.cq.Q);
+    if (placed < 0) return false;
+    // leftovers (no room anywhere): relax them inline, one chunk at a time
+    const unsigned act_mask = __ballot_sync(kFullMask, act);
+    const int rank = __popc(act_mask & ((1u << lane) - 1u));
+    unsigned left = __ballot_sync(kFullMask, act && rank >= placed);
+    while (left) {
+      const int src_lane = __ffs(left) - 1;
+      left &= left - 1;
+      const unsigned cid = __shfl_sync(kFullMask, id, src_lane);
+      int beg = 0, deg = 0;
+      long long lab = 0;
+      if (lane == 0) {
+        const int4 ct = a.chunk_tab[cid];
+        beg = ct.y;
+        deg = ct.z - ct.y;
+        lab = ld_relaxed_s64(&a.label[ct.x]);
+      }
+      if (!relax_merged(a, 1, beg, deg, lab, lane, home, wc)) return false;
+      __syncwarp();
+      if (lane == 0) atom_add_release_s32(&a.ctl->inflight, -1);
+    }
+  }
+  return true;
+}
+
+// Dequeue from sub-queue q of qs, taking a share of its items proportional
+// to the warps that serve it.
+__device__ __forceinline__ int dequeue_share(const QueueSet& qs, int q, int max_items,
+                                             int share, int lane, unsigned* item,
+                                             long long spin_limit) {
+  int cnt = 0;
+  if (lane == 0) cnt = ld_relaxed_s32(&qs.meta[q].count);
+  cnt = __shfl_sync(kFullMask, cnt, 0);
+  if (cnt <= 0) return 0;
+  const int want = min(max_items, max(1, (cnt + share - 1) / share));
+  return wq_dequeue_warp(qs, q, want, lane, item, spin_limit);
+}
+
+__global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int home = (blockIdx.x * a.queues_per_cta + wid % a.queues_per_cta) % a.qs.Q;
+  const int chome = blockIdx.x % a.cq.Q;
+  const int share = max(1, nwarps / a.queues_per_cta);
+  WarpCounters wc;
+  const unsigned long long t_start = globaltimer_ns();
+  unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
+  int idle = 0;
+  bool timed_out = false;
+
+  for (;;) {
+    unsigned item = 0;
+    // hub chunks first (they sit on the critical path), then the own
+    // vertex sub-queue, then stealing
+    bool is_chunk = true;
+    int got = dequeue_share(a.cq, chome, 1, 1, lane, &item, a.spin_limit);
+    if (got == 0) {
+      is_chunk = false;
+      got = dequeue_share(a.qs, home, a.batch_items, share, lane, &item, a.spin_limit);
+    }
+    if (got == 0) {
+      rng = rng * 1664525u + 1013904223u;
+      int q = probe_queues(a.cq, (int)(rng % (unsigned)a.cq.Q), chome, lane);
+      if (q >= 0) {
+        is_chunk = true;
+        got = dequeue_share(a.cq, q, 1, 1, lane, &item, a.spin_limit);
+      } else {
+        q = probe_queues(a.qs, (int)((rng >> 7) % (unsigned)a.qs.Q), home, lane);
+        if (q >= 0) got = dequeue_share(a.qs, q, a.batch_items, share, lane, &item, a.spin_limit);
+      }
+      if (got > 0) ++wc.steal;
+    }
+    if (got < 0) { timed_out = true; break; }
+    if (got == 0) {
+      int done = 0;
+      if (lane == 0)
+        done = (ld_acquire_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
+      if (__shfl_sync(kFullMask, done, 0)) break;
+      ++wc.idle;
+      __nanosleep(min(32u << min(idle, 6), 2048u));
+      ++idle;
+      if ((idle & 31) == 0 &&
+          (long long)(globaltimer_ns() - t_start) > a.time_limit_ns) {
+        timed_out = true;
+        break;
+      }
+      continue;
+    }
+    idle = 0;
+    wc.deq += (lane == 0) ? (unsigned long long)got : 0ull;
+    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
+
+    int beg = 0, deg = 0, nch = 0, c0 = 0;
+    long long lab = 0;
+    if (lane < got) {
+      if (is_chunk) {
+        const int4 ct = a.chunk_tab[item];
+        beg = ct.y;
+        deg = ct.z - ct.y;
+        lab = ld_relaxed_s64(&a.label[ct.x]);
+      } else {
+        const unsigned u = item;
+        // clear the in-queue bit, then read the label (see relax_merged)
+        atomicAnd(&a.bitmap[u >> 5], ~(1u << (u & 31u)));
+        fence_acq_rel_gpu();
+        lab = ld_relaxed_s64(&a.label[u]);
+        beg = __ldg(&a.row_ptr[u]);
+        deg = __ldg(&a.row_ptr[u + 1]) - beg;
+        if (deg > a.hub_degree) {
+          nch = (deg + a.chunk_edges - 1) / a.chunk_edges;
+          c0 = __ldg(&a.hub_chunk0[u]);
+          deg = 0;
+        }
+      }
+    }
+    if (__any_sync(kFullMask, nch > 0)) {
+      if (!push_chunks(a, nch, c0, lane, home, chome, wc)) { timed_out = true; break; }
+    }
+    if (!relax_merged(a, got, beg, deg, lab, lane, home, wc)) {
+      timed_out = true;
+      break;
+    }
+    // retire the batch: the warp's label writes and enqueues are ordered
+    // before the decrement (syncwarp, then a release add)
+    __syncwarp();
+    int stop = 0;
+    if (lane == 0) {
+      atom_add_release_s32(&a.ctl->inflight, -got);
+      stop = ld_relaxed_s32(&a.ctl->stop);
+    }
+    if (__shfl_sync(kFullMask, stop, 0)) break;
+  }
+  if (timed_out && lane == 0) raise_status(a.ctl, kStTimeout);
+
+  wc.upd = warp_sum_u64(wc.upd);
+  if (lane == 0) {
+    if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], wc.deq);
+    if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], wc.rel);
+    if (wc.upd) atomicAdd(&a.ctl->ctr[kCtrUpd], wc.upd);
+    if (wc.enq) atomicAdd(&a.ctl->ctr[kCtrEnq], wc.enq);
+    if (wc.steal) atomicAdd(&a.ctl->ctr[kCtrSteal], wc.steal);
+    if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], wc.chunk);
+    if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], wc.idle);
+  }
+  __syncthreads();
+
+  // epilogue: unpack this CTA's slice of the labels.  Every warp left its
+  // loop after seeing the in-flight count at zero (acquire), so every label
+  // write has happened; after an early stop the results are unspecified.
+  const long long per = ((long long)a.V + gridDim.x - 1) / gridDim.x;
+  const long long lo = per * blockIdx.x;
+  const long long hi = min((long long)a.V, lo + per);
+  for (long long v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+    const long long l = ld_relaxed_s64(&a.label[v]);
+    a.dist[v] = label_dist(l);
+    if (a.hops) a.hops[v] = (int)label_hops(l);
+    if (a.pred) a.pred[v] = -1;
+  }
+}
+
+// Labels start at (INT32_MAX, 0xffffffff), the source at (0, 0); the source
+// is queued in vertex sub-queue 0.  If the previous run ended early
+// (last_status != 0) the bitmap and all sub-queues are reset first; a clean
+// run leaves every sub-queue empty and every bit clear.
+__global__ void sssp_init_kernel(SsspArgs a) {
+  const bool dirty = a.ctl->last_status != 0;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < a.V; v += nth) a.label[v] = (v == a.src) ? 0LL : kInfLabel;
+  const long long sw = a.src >> 5;
+  const unsigned sbit = 1u << (a.src & 31);
+  if (dirty) {
+    const long long words = ((long long)a.V + 31) / 32;
+    for (long long i = tid; i < words; i += nth) a.bitmap[i] = (i == sw) ? sbit : 0u;
+    const long long nslots = (long long)a.qs.Q << a.qs.cap_log2;
+    for (long long i = tid; i < nslots; i += nth)
+      a.qs.slots[i] = (i == 0) ? ((1ull << 32) | (unsigned)a.src) : 0ull;
+    const long long ncslots = (long long)a.cq.Q << a.cq.cap_log2;
+    for (long long i = tid; i < ncslots; i += nth) a.cq.slots[i] = 0ull;
+    for (long long q = tid; q < a.qs.Q; q += nth) {
+      a.qs.meta[q].count = (q == 0) ? 1 : 0;
+      a.qs.meta[q].head = 0;
+      a.qs.meta[q].tail = (q == 0) ? 1 : 0;
+    }
+    for (long long q = tid; q < a.cq.Q; q += nth) {
+      a.cq.meta[q].count = 0;
+      a.cq.meta[q].head = 0;
+      a.cq.meta[q].tail = 0;
+    }
+  } else if (tid == 0) {
+    a.bitmap[sw] = sbit;
+    QueueMeta* m = a.qs.meta;
+    const unsigned long long p = m->tail;
+    const unsigned lap = (unsigned)(p >> a.qs.cap_log2);
+    a.qs.slots[p & ((1ull << a.qs.cap_log2) - 1)] =
+        ((unsigned long long)(2u * lap + 1u) << 32) | (unsigned)a.src;
+    m->tail = p + 1;
+    m->count = 1;
+  }
+  if (tid == 0) {
+    a.ctl->inflight = 1 + a.phantom;
+    a.ctl->status = 0;
+    a.ctl->stop = 0;
+    for (int i = 0; i < 8; ++i) a.ctl->ctr[i] = 0;
+  }
+}
+
+// Status code of the run, also kept for the next run's init.
+__global__ void sssp_finalize_kernel(Control* ctl, int32_t* status_dev) {
+  const int st = ctl->status;
+  int code = BFQ_OK;
+  if (st & (kStTimeout | kStQueue)) code = BFQ_ERR_TIMEOUT;
+  else if (st & kStNegCycle) code = BFQ_NEG_CYCLE;
+  else if (st & kStRange) code = BFQ_RANGE;
+  ctl->last_status = code;
+  if (status_dev) *status_dev = code;
+}
+
+// Predecessor post-pass: for each reached u and edge (u, v, w) with
+// dist[u] + w == dist[v] and hops[u] + 1 == hops[v], pred[v] = u.  Any such u
+// is valid; following pred strictly lowers hops, so the tree is acyclic.
+__global__ void sssp_pred_kernel(const int* __restrict__ row_ptr, const int2* __restrict__ adj,
+                                 const long long* __restrict__ label, int V, int* pred,
+                                 const Control* ctl) {
+  if (ctl->last_status != 0) return;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long u = warp; u < V; u += nw) {
+    const long long lu = label[u];
+    if (label_dist(lu) == kInf32) continue;
+    const int b = row_ptr[u], e = row_ptr[u + 1];
+    for (int i = b + lane; i < e; i += 32) {
+      const int2 cw = adj[i];
+      const long long nd = (long long)label_dist(lu) + cw.y;
+      if (nd >= kInf32) continue;
+      const long long lv = label[cw.x];
+      if (label_dist(lv) == (int)nd && label_hops(lv) == label_hops(lu) + 1u) pred[cw.x] = (int)u;
+    }
+  }
+}
+
+__global__ void reached_edges_kernel(const int* __restrict__ row_ptr,
+                                     const long long* __restrict__ label, int V,
+                                     unsigned long long* out2) {
+  unsigned long long m = 0, r = 0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (label_dist(label[v]) != kInf32) {
+      m += (unsigned long long)(row_ptr[v + 1] - row_ptr[v]);
+      ++r;
+    }
+  }
+  m = warp_sum_u64(m);
+  r = warp_sum_u64(r);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out2[0], m);
+    atomicAdd(&out2[1], r);
+  }
+}
+
+__global__ void pack_adj_kernel(const int* __restrict__ col, const int* __restrict__ w,
+                                int2* __restrict__ adj, long long E) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < E;
+       i += (long long)gridDim.x * blockDim.x)
+    adj[i] = make_int2(col[i], w[i]);
+}
+
+__global__ void validate_csr_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                    int V, long long E, int* bad) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  if (tid == 0 && (row_ptr[0] != 0 || (long long)row_ptr[V] != E)) atomicOr(bad, 1);
+  for (long long v = tid; v < V; v += nth)
+    if (row_ptr[v + 1] < row_ptr[v]) atomicOr(bad, 2);
+  for (long long i = tid; i < E; i += nth)
+    if (col[i] < 0 || col[i] >= V) atomicOr(bad, 4);
+}
+
+__global__ void queue_reset_kernel(QueueSet qs) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long n = (long long)qs.Q << qs.cap_log2;
+  for (long long i = tid; i < n; i += nth) qs.slots[i] = 0ull;
+  for (long long q = tid; q < qs.Q; q += nth) {
+    qs.meta[q].count = 0;
+    qs.meta[q].head = 0;
+    qs.meta[q].tail = 0;
+  }
+}
+
+}  // namespace
+
+int sssp_max_ctas_per_sm(int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_persistent_kernel, block, 0) !=
+      cudaSuccess)
+    return 1;
+  return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,
+                        int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
+                        cudaStream_t s) {
+  sssp_init_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a);
+  if (ev0) cudaEventRecord(ev0, s);
+  sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  if (ev1) cudaEventRecord(ev1, s);
+  sssp_finalize_kernel<<<1, 1, 0, s>>>(a.ctl, status_dev);
+  if (a.pred)
+    sssp_pred_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a.row_ptr, a.adj, a.label, a.V,
+                                                                 a.pred, a.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reached_edges(const int* row_ptr, const long long* label, int V,
+                                 unsigned long long* out2, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  reached_edges_kernel<<<1024, 256, 0, s>>>(row_ptr, label, V, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_adj(const int* col, const int* w, int2* adj, long long E, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  pack_adj_kernel<<<2048, 256, 0, s>>>(col, w, adj, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csr(const int* row_ptr, const int* col, int V, long long E, int* bad,
+                                cudaStream_t s) {
+  validate_csr_kernel<<<1024, 256, 0, s>>>(row_ptr, col, V, E, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s) {
+  queue_reset_kernel<<<1024, 256, 0, s>>>(qs);
+  return cudaGetLastError();
+}
+
+}  // namespace bfq

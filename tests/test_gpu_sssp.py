@@ -1,0 +1,245 @@
+"""Parity of the CUDA SSSP path (through the C ABI) with the oracle: dist,
+hops and status bit-exact, predecessor trees checked by invariant."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_21826_gb300 import bfq, synth
+from tests import gpu_util, helpers
+
+pytestmark = pytest.mark.gpu
+INF = helpers.INF
+
+
+def _compare(g, src, res, check_pred=False):
+    st, d, h, p = res
+    ost, od, oh, _ = oracle.spfa(g.row_ptr, g.col, g.w, src)
+    assert st == ost, (st, ost)
+    if ost == oracle.OK:
+        bad = np.nonzero(d != od)[0]
+        assert bad.size == 0, f"{bad.size} dist mismatches, first {bad[:5]}: {d[bad[:5]]} vs {od[bad[:5]]}"
+        assert np.array_equal(h, oh), "hops mismatch"
+        if check_pred:
+            assert oracle.check_pred(g.row_ptr, g.col, g.w, src, d, p)
+    return ost
+
+
+@pytest.mark.parametrize("path", helpers.golden_files(), ids=lambda p: p.split("/")[-1])
+def test_golden(path):
+    g, exp = helpers.load_golden(path)
+    st, d, h, p = gpu_util.sssp(g, 0, want_pred=True)
+    assert st == exp["status"]
+    if "dist" in exp:
+        assert d.tolist() == exp["dist"] and h.tolist() == exp["hops"]
+        assert oracle.check_pred(g.row_ptr, g.col, g.w, 0, d, p)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_random_with_cycles(seed):
+    rng = np.random.default_rng(seed)
+    V = int(rng.integers(1, 3000))
+    E = int(rng.integers(0, 6 * V + 1))
+    g = synth.random_graph(V, E, seed=500 + seed, wlo=-3, whi=40)
+    _compare(g, 0, gpu_util.sssp(g, 0))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_potential(seed):
+    rng = np.random.default_rng(100 + seed)
+    V = int(rng.integers(2000, 40000))
+    g = synth.random_potential_graph(V, 6 * V, seed=seed)
+    assert _compare(g, 0, gpu_util.sssp(g, 0, want_pred=True), check_pred=True) == oracle.OK
+
+
+def test_tie_heavy():
+    g = synth.random_potential_graph(30000, 200000, seed=3, wmax=1, pmax=3)
+    _compare(g, 0, gpu_util.sssp(g, 0, want_pred=True), check_pred=True)
+
+
+def test_grid4k_full():
+    g = synth.workload_grid4k()
+    h = gpu_util.create(g)
+    try:
+        res = gpu_util.run(h, g.V, 0, want_pred=True)
+        _compare(g, 0, res, check_pred=True)
+        stats = bfq.bfq_get_stats(h)
+        assert stats["m_reached"] == oracle.reached_edges(g.row_ptr, res[1]) == g.E
+        assert stats["reached"] == g.V
+        assert stats["relaxed"] >= g.E and stats["dequeued"] >= g.V
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_road_twin_all_sources():
+    g = synth.road_graph(256, seed=7)
+    h = gpu_util.create(g)
+    try:
+        for s in g.sources:
+            _compare(g, int(s), gpu_util.run(h, g.V, int(s), want_pred=True), check_pred=True)
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_road1m_full_all_sources():
+    g = synth.workload_road1m()
+    h = gpu_util.create(g)
+    try:
+        for s in g.sources:
+            _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("scale", [12, 16])
+def test_rmat_twins(scale):
+    g = synth.workload_rmat(scale)
+    h = gpu_util.create(g)
+    try:
+        for s in g.sources:
+            _compare(g, int(s), gpu_util.run(h, g.V, int(s), want_pred=True), check_pred=True)
+        assert bfq.bfq_get_stats(h)["hub_chunks"] > 0 or np.diff(g.row_ptr).max() <= 512
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_rmat22_full_all_sources():
+    g = synth.workload_rmat(22)
+    h = gpu_util.create(g)
+    try:
+        for s in g.sources:
+            st, d, hh, _ = gpu_util.run(h, g.V, int(s))
+            # exact against Dijkstra through the potential transform (fast),
+            # and against the label-correcting oracle for the first source
+            db, hb = oracle.dijkstra(g.row_ptr, g.col, g.base_w, int(s))
+            ed, eh = helpers.shifted_expectation(db, hb, g.potential, int(s))
+            assert st == bfq.OK
+            assert np.array_equal(d, ed) and np.array_equal(hh, eh)
+        _compare(g, int(g.sources[0]), gpu_util.run(h, g.V, int(g.sources[0])))
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("tune", [
+    dict(hub_degree=32, chunk_edges=32),
+    dict(batch_items=1),
+    dict(queues_per_cta=4),
+    dict(ctas_per_sm=1),
+    dict(hub_degree=64, chunk_edges=32, batch_items=4, queues_per_cta=2),
+], ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+def test_tunes(tune):
+    g = synth.workload_rmat(14)
+    t = bfq.make_tune(**tune)
+    h = gpu_util.create(g, t)
+    try:
+        for s in g.sources[:2]:
+            _compare(g, int(s), gpu_util.run(h, g.V, int(s), want_pred=True), check_pred=True)
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_star_hub_chunks():
+    V = 200_000
+    w = np.random.default_rng(1).integers(-1000, 1000, size=V - 1).astype(np.int32)
+    g = synth.star_graph(V, w)
+    st, d, h, p = gpu_util.sssp(g, 0, want_pred=True)
+    assert st == bfq.OK and d[0] == 0 and np.array_equal(d[1:], w)
+    assert np.all(h[1:] == 1) and np.all(p[1:] == 0)
+
+
+def test_long_path():
+    V = 20_000
+    w = np.random.default_rng(2).integers(-5, 9, size=V - 1).astype(np.int32)
+    g = synth.path_graph(V, w)
+    st, d, h, _ = gpu_util.sssp(g, 0)
+    assert st == bfq.OK
+    assert np.array_equal(d, np.r_[0, np.cumsum(w)]) and np.array_equal(h, np.arange(V))
+
+
+def test_single_vertex_and_no_edges():
+    g = synth.Graph("one", np.array([0, 0], np.int32), np.zeros(0, np.int32),
+                    np.zeros(0, np.int32), np.array([0], np.int32))
+    st, d, h, p = gpu_util.sssp(g, 0, want_pred=True)
+    assert st == bfq.OK and d.tolist() == [0] and h.tolist() == [0] and p.tolist() == [-1]
+    rp = np.zeros(1001, np.int32)
+    g = synth.Graph("empty", rp, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                    np.array([0], np.int32))
+    st, d, h, _ = gpu_util.sssp(g, 500)
+    assert st == bfq.OK and d[500] == 0 and np.sum(d == INF) == 1000
+
+
+def test_device_resident_input():
+    g = synth.rmat_graph(13, 8, seed=4)
+    _compare(g, int(g.sources[0]), gpu_util.sssp(g, int(g.sources[0]), on_device=True))
+
+
+def test_cycle_then_clean_on_one_handle():
+    """A run that stops on a negative cycle leaves the queues dirty; the next
+    run on the same handle must reset them and still be exact."""
+    base = synth.grid_graph(60, 60, seed=5)
+    V = base.V
+    u = base.tails().astype(np.int64)
+    v = base.col.astype(np.int64)
+    rp, col, order = synth.csr_from_edges(2 * V, np.r_[u, u + V], np.r_[v, v + V],
+                                          return_order=True)
+    two = synth.Graph("two", rp, col, np.r_[base.w, base.w][order].astype(np.int32),
+                      np.array([V], np.int32), base_w=np.r_[base.base_w, base.base_w][order],
+                      potential=np.r_[base.potential, base.potential])
+    g = synth.plant_negative_cycle(two, 5, seed=3, reachable_from=[V])   # in copy 2
+    assert np.all(g.cycle >= V)
+    h = gpu_util.create(g)
+    try:
+        for src in (V, 0, V + 17, 5, 0):
+            res = gpu_util.run(h, g.V, src)
+            ost = _compare(g, src, res)
+            assert ost == (oracle.NEG_CYCLE if src >= V else oracle.OK)
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_many_runs_reuse_state():
+    g = synth.workload_rmat(15)
+    h = gpu_util.create(g)
+    try:
+        rng = np.random.default_rng(0)
+        cand = np.nonzero(np.diff(g.row_ptr) > 0)[0]
+        for s in rng.choice(cand, size=12, replace=False):
+            _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_bad_arguments():
+    g = synth.grid_graph(8, 8, seed=1)
+    h = gpu_util.create(g)
+    try:
+        import torch
+        d = torch.empty(g.V, dtype=torch.int32, device="cuda")
+        with pytest.raises(bfq.BfqError) as e:
+            bfq.bfq_sssp(h, g.V, d)
+        assert e.value.code == bfq.ERR_INVALID
+        with pytest.raises(bfq.BfqError):
+            bfq.bfq_sssp(h, 0, None)
+        bad_col = g.col.copy()
+        bad_col[3] = g.V
+        with pytest.raises(bfq.BfqError):
+            bfq.bfq_graph_create(g.row_ptr, bad_col, g.w)
+        st, dd, _, _ = gpu_util.run(h, g.V, 0)          # handle still usable
+        assert st == bfq.OK
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_timeout_leaves_context_usable():
+    """An in-flight count that nothing can retire (test hook) keeps the
+    persistent kernel idle until its time limit; the run must end with
+    BFQ_ERR_TIMEOUT, and the device must serve exact queries afterwards."""
+    g = synth.workload_rmat(12)
+    t = bfq.make_tune(time_limit_ms=30, test_phantom_items=1)
+    h = gpu_util.create(g, t)
+    try:
+        with pytest.raises(bfq.BfqError) as e:
+            gpu_util.run(h, g.V, int(g.sources[0]))
+        assert e.value.code == bfq.ERR_TIMEOUT
+    finally:
+        bfq.bfq_graph_destroy(h)
+    _compare(g, int(g.sources[0]), gpu_util.sssp(g, int(g.sources[0])))
