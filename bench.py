@@ -39,17 +39,19 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="rmat22", choices=["rmat22", "road1m", "grid4k"])
+    p.add_argument("--rmat-scale", type=int, default=22,
+                   help="scale of the rmat22 workload (smaller only for profiling captures)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
 
-def load_workload(name):
+def load_workload(name, rmat_scale=22):
     from paper_2608_21826_gb300 import synth
     if name == "rmat22":
-        g = synth.workload_rmat(22)
-        desc = "rmat22_ef16: R-MAT scale 22, edge factor 16, (.57,.19,.19,.05), dedup, " \
-               "w U[1,255] + potentials U[0,128], 4 sources"
+        g = synth.workload_rmat(rmat_scale)
+        desc = f"rmat{rmat_scale}_ef16: R-MAT scale {rmat_scale}, edge factor 16, " \
+               "(.57,.19,.19,.05), dedup, w U[1,255] + potentials U[0,128], 4 sources"
     elif name == "road1m":
         g = synth.workload_road1m()
         desc = "road1m: 1024^2 grid, 10% edges dropped, 1% shortcuts, w U[1,1000] + " \
@@ -181,7 +183,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    g, desc = load_workload(args.workload)
+    g, desc = load_workload(args.workload, args.rmat_scale)
     srcs = [int(s) for s in g.sources]
     for i in range(args.warmup):
         oracle.spfa(g.row_ptr, g.col, g.w, srcs[i % len(srcs)])
@@ -219,7 +221,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2608_21826_gb300 import bfq
 
-    g, desc = load_workload(args.workload)
+    g, desc = load_workload(args.workload, args.rmat_scale)
     h = bfq.bfq_graph_create(g.row_ptr, g.col, g.w)
     V = g.V
     srcs = [int(s) for s in g.sources]
