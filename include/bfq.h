@@ -157,6 +157,31 @@ int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
 /* Counters of the last run on g (synchronises the device). */
 int bfq_get_stats(bfq_graph_t g, bfq_stats* out);
 
+/* One query that allocates nothing (the paper has no counterpart; this is a
+ * library facility).  It is meant for callers that cannot allocate device
+ * memory when they need a query: code running while a stream is captured
+ * into a CUDA graph (an allocation there breaks the capture), programs that
+ * fix their memory budget at start-up, or code living inside another
+ * framework's memory arena.  All working memory (labels, in-queue bitmap,
+ * sub-queues, control block) comes from one static 16 MiB array in device
+ * memory that every GPU loading this library holds until the process exits.
+ *   row_ptr: int32[V+1], adj: int32[2E] interleaved (col, w) pairs, 8-byte
+ *   aligned; dist: int32[V]; hops: int32[V] or NULL; status_dev: one int32.
+ *   All are caller-owned device pointers.
+ * Limits: 1 <= V <= 524288 and 0 <= E < 2^31; larger graphs are rejected
+ * with BFQ_ERR_INVALID and a message.  Hub splitting is off on this path.
+ * Asynchronous on `stream`: returns BFQ_OK once enqueued; the run's status
+ * (BFQ_OK, BFQ_NEG_CYCLE, BFQ_RANGE, BFQ_ERR_TIMEOUT, or BFQ_ERR_INVALID if
+ * the CSR fails the device-side check) is written to *status_dev.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array and clears
+ * the parts it needs, so calls whose GPU work overlaps (on two streams, or
+ * from two threads) race and must be serialised by the caller. */
+int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
+                     int64_t E, int32_t src, int32_t* dist, int32_t* hops,
+                     int32_t* status_dev, void* stream);
+
 /* ---- standalone Broker Queue (Sec. III-A, Algorithm 1; Sec. IV workloads) */
 /* A ring of `capacity` int32 items (rounded up to a power of two for the
  * warp variant), variant = BFQ_QUEUE_*. */

@@ -60,6 +60,7 @@ _SIGNATURES = {
     "bfq_sssp": ([_VP, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
     "bfq_sssp_async": ([_VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "bfq_get_stats": ([_VP, ctypes.POINTER(Stats)], ctypes.c_int),
+    "bfq_sssp_noalloc": ([_VP, _VP, _I32, _I64, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
     "bfq_queue_create": ([ctypes.POINTER(_VP), _I64, _I32], ctypes.c_int),
     "bfq_queue_destroy": ([_VP], ctypes.c_int),
     "bfq_queue_reset": ([_VP, _VP], ctypes.c_int),
@@ -192,6 +193,15 @@ def bfq_get_stats(g) -> dict:
     s = Stats()
     _check(lib().bfq_get_stats(g, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+
+
+def bfq_sssp_noalloc(row_ptr, adj, V: int, E: int, src: int, dist, hops=None, status_dev=None,
+                     stream=None) -> int:
+    """Query without any allocation (fixed static scratch, V <= 524288); the
+    status lands in status_dev (device int32).  Returns OK once enqueued."""
+    return _check(lib().bfq_sssp_noalloc(_ptr(row_ptr), _ptr(adj), int(V), int(E), int(src),
+                                         _ptr(dist), _ptr(hops), _ptr(status_dev),
+                                         _stream(stream)))
 
 
 # ---- standalone queue ----------------------------------------------------------

@@ -78,5 +78,8 @@ cudaError_t launch_pack_adj(const int* col, const int* w, int2* adj, long long E
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, int V, long long E,
                                 int* bad, cudaStream_t s);
 cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s);
+// The persistent relaxation kernel alone (no init, finalize or pred pass).
+cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
+                                        cudaStream_t s);
 
 }  // namespace bfq

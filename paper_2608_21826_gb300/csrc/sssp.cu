@@ -538,4 +538,10 @@ cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
+                                        cudaStream_t s) {
+  sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace bfq
