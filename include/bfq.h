@@ -95,7 +95,11 @@ typedef struct bfq_tune {
   int32_t test_phantom_items; /* test hook, 0 in normal use: in-flight items
                                that no queued item backs, so a run can only
                                end through time_limit_ms (BFQ_ERR_TIMEOUT) */
-  int32_t reserved[6];
+  int32_t share_div;        /* a warp dequeues ceil(count / share_div) items
+                               of a sub-queue holding count (<= batch_items);
+                               0 = the number of warps serving it           */
+  int32_t chunk_batch;      /* hub chunks a warp dequeues at once (1..32)    */
+  int32_t reserved[4];
 } bfq_tune;
 
 /* Counters of the last finished run on a graph handle (summed over warps). */
@@ -113,7 +117,8 @@ typedef struct bfq_stats {
   double kernel_ms;       /* duration of the persistent relaxation kernel,
                              from CUDA events recorded around its launch on
                              the caller's stream                            */
-  int64_t reserved[5];
+  int64_t idle_polls;     /* polls by warps that found no work               */
+  int64_t reserved[4];
 } bfq_stats;
 
 /* ---- errors ------------------------------------------------------------ */

@@ -3,11 +3,13 @@
 Each ``bfq_*`` function here marshals its arguments (numpy arrays, torch
 tensors, raw pointers, streams) and calls the C entry point of the same name;
 all computation runs in the library's CUDA kernels.  There is no fallback:
-if the library cannot be built or loaded, ``lib()`` raises.
+if the library cannot be built or loaded, ``lib()`` raises.  BFQ_LIBRARY may
+name another build of the library to load instead of the in-tree one.
 """
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
@@ -32,7 +34,8 @@ class Tune(ctypes.Structure):
                 ("hub_degree", ctypes.c_int32), ("chunk_edges", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("time_limit_ms", ctypes.c_int64),
                 ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("V", ctypes.c_int64), ("E", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("queues", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
-                ("kernel_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 5)]
+                ("kernel_ms", ctypes.c_double), ("idle_polls", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 _VP = ctypes.c_void_p
@@ -80,7 +84,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = os.environ.get("BFQ_LIBRARY") or _build.build()
             handle = ctypes.CDLL(path)
             for name, (args, res) in _SIGNATURES.items():
                 f = getattr(handle, name)

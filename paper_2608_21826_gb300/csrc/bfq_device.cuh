@@ -28,7 +28,6 @@ namespace bfq {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kInf32 = 2147483647;
-constexpr long long kInfLabel = 0x7fffffffffffffffLL;   // (INT32_MAX, 0xffffffff)
 
 // Status bits collected while a run executes.
 enum : int {
@@ -95,19 +94,35 @@ __device__ __forceinline__ int atom_add_release_s32(int* p, int v) {
                : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
 }
+// fire-and-forget add (no value returned, so the warp does not wait)
+__device__ __forceinline__ void red_add_relaxed_s32(int* p, int v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// Pack a (dist, hops) label so that signed 64-bit order is lexicographic
-// order: dist in the high word (signed), hops in the low word (unsigned).
+// Label word of a vertex: dist (int32) in the high half, hops (31 bits) in
+// bits 1..31, and the in-queue flag in bit 0.  With the flag cleared, signed
+// 64-bit order is lexicographic (dist, hops) order, so comparing words
+// compares labels.  Keeping the flag in the label word lets a producer lower
+// the label and claim the enqueue in one compare-and-swap, and a consumer
+// clear the flag and read the label in one atomicAnd: a single memory
+// location, so no fence is needed to order the two.
+constexpr long long kQueuedBit = 1LL;
+constexpr long long kInfLabel = 0x7ffffffffffffffeLL;   // (INT32_MAX, 2^31-1), not queued
+
 __device__ __forceinline__ long long pack_label(int dist, unsigned hops) {
-  return (long long)(((unsigned long long)(unsigned)dist << 32) | hops);
+  return (long long)(((unsigned long long)(unsigned)dist << 32) |
+                     ((unsigned long long)hops << 1));
 }
 __device__ __forceinline__ int label_dist(long long l) { return (int)(l >> 32); }
-__device__ __forceinline__ unsigned label_hops(long long l) { return (unsigned)l; }
+__device__ __forceinline__ unsigned label_hops(long long l) {
+  return ((unsigned)(unsigned long long)l) >> 1;
+}
+__device__ __forceinline__ long long label_key(long long l) { return l & ~kQueuedBit; }
 
 // ---------------------------------------------------------------------------
 // warp-aggregated Broker Queue (sub-queue of the SSSP worklist)
@@ -148,9 +163,9 @@ struct QueueSet {
 // granted and will free the slot.  Every wait is on an earlier ticket that is
 // already granted, hence no cycle of waits.
 __device__ __forceinline__ int wq_reserve(QueueMeta* m, int want, bool is_deq, int cap,
-                                          unsigned long long* pos) {
+                                          unsigned long long* pos, int c_hint = -1) {
   int got = 0;
-  int c = ld_relaxed_s32(&m->count);
+  int c = c_hint >= 0 ? c_hint : ld_relaxed_s32(&m->count);
   for (;;) {
     int room = is_deq ? c : cap - c;
     if (room <= 0) break;
@@ -204,10 +219,11 @@ __device__ __forceinline__ bool wq_take(unsigned long long* qslots, int cap_log2
 // Warp-collective dequeue of up to `want` items from sub-queue q.  Lanes
 // [0, got) receive an item.  Returns got, or -1 if a ticket wait ran out.
 __device__ __forceinline__ int wq_dequeue_warp(const QueueSet& qs, int q, int want, int lane,
-                                               unsigned* item, long long spin_limit) {
+                                               unsigned* item, long long spin_limit,
+                                               int c_hint = -1) {
   unsigned long long pos = 0;
   int got = 0;
-  if (lane == 0) got = wq_reserve(qs.meta + q, want, true, 1 << qs.cap_log2, &pos);
+  if (lane == 0) got = wq_reserve(qs.meta + q, want, true, 1 << qs.cap_log2, &pos, c_hint);
   got = __shfl_sync(kFullMask, got, 0);
   if (got == 0) return 0;
   pos = __shfl_sync(kFullMask, pos, 0);

@@ -30,8 +30,7 @@ enum CtrIndex { kCtrDeq = 0, kCtrRel, kCtrUpd, kCtrEnq, kCtrSteal, kCtrChunk, kC
 struct SsspArgs {
   const int* row_ptr;           // [V+1]
   const int2* adj;              // [E] (col, w)
-  long long* label;             // [V] packed (dist, hops)
-  unsigned* bitmap;             // [ceil(V/32)] in-queue bits
+  long long* label;             // [V] packed (dist, hops, in-queue flag)
   QueueSet qs;                  // vertex sub-queues
   QueueSet cq;                  // hub edge-chunk sub-queues
   const int* hub_chunk0;        // [V] first chunk-table entry of a hub (read for hubs only)
@@ -44,6 +43,8 @@ struct SsspArgs {
   int src;
   int batch_items;
   int queues_per_cta;
+  int share_div;                // a warp takes ceil(count / share_div) items (0: warps per queue)
+  int chunk_batch;              // hub chunks a warp takes at once
   int hub_degree;
   int chunk_edges;
   long long spin_limit;
@@ -68,7 +69,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 // Kernels launchers (sssp.cu)
 int sssp_max_ctas_per_sm(int block);
-// init, persistent run (bracketed by ev0/ev1 when given), finalize, pred.
+// init, persistent run (bracketed by ev0/ev1 when given), epilogue, pred.
 cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,
                         int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
                         cudaStream_t s);
@@ -78,8 +79,12 @@ cudaError_t launch_pack_adj(const int* col, const int* w, int2* adj, long long E
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, int V, long long E,
                                 int* bad, cudaStream_t s);
 cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s);
-// The persistent relaxation kernel alone (no init, finalize or pred pass).
+// The persistent relaxation kernel alone (no init, epilogue or pred pass).
 cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
                                         cudaStream_t s);
+// The epilogue alone: unpack labels to dist/hops (pred to -1) and write the
+// status code; `bad` (nullable, device) forces BFQ_ERR_INVALID when non-zero.
+cudaError_t launch_sssp_epilogue(const SsspArgs& a, LaunchShape shape, int32_t* status_dev,
+                                 const int* bad, cudaStream_t s);
 
 }  // namespace bfq

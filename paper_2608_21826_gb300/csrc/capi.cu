@@ -47,7 +47,6 @@ struct bfq_graph {
   int* row_ptr = nullptr;
   int2* adj = nullptr;
   long long* label = nullptr;
-  unsigned* bitmap = nullptr;
   QueueSet qs{};
   QueueSet cq{};
   int* hub_chunk0 = nullptr;
@@ -98,6 +97,8 @@ int bfq_tune_default(bfq_tune* t) {
   t->spin_limit = 1LL << 22;
   t->time_limit_ms = 20000;
   t->l2_persist_pct = 0;
+  t->share_div = 2;
+  t->chunk_batch = 4;
   return BFQ_OK;
 }
 
@@ -114,6 +115,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (in->time_limit_ms) out->time_limit_ms = in->time_limit_ms;
   if (in->l2_persist_pct) out->l2_persist_pct = in->l2_persist_pct;
   out->test_phantom_items = in->test_phantom_items;
+  if (in->share_div) out->share_div = in->share_div;
+  if (in->chunk_batch) out->chunk_batch = in->chunk_batch;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 in this build");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -125,7 +128,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (out->hub_degree < out->chunk_edges)
     return invalid("bfq_tune: hub_degree must be >= chunk_edges");
   if (out->spin_limit < 1 || out->time_limit_ms < 1 || out->ctas_per_sm < 0 ||
-      out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0)
+      out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0 ||
+      out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32)
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -229,7 +233,7 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   g->run_shape = {sms * per_sm, block};
   g->init_shape = {sms * 4, 256};
 
-  // workspace: labels, in-queue bitmap, vertex and chunk sub-queues
+  // workspace: labels (with in-queue flags), vertex and chunk sub-queues
   const int Q = g->run_shape.grid * g->tune.queues_per_cta;
   const long long per_q = (2LL * V + Q - 1) / Q;
   int cap_log2 = std::max(10, ceil_log2(per_q));
@@ -239,9 +243,7 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   const long long per_qc = (4LL * g->n_chunks + Qc - 1) / Qc;
   g->cq.Q = Qc;
   g->cq.cap_log2 = std::max(8, ceil_log2(std::max(1LL, per_qc)));
-  const long long words = ((long long)V + 31) / 32;
   G_TRY(g->alloc((void**)&g->label, sizeof(long long) * (size_t)V));
-  G_TRY(g->alloc((void**)&g->bitmap, sizeof(unsigned) * (size_t)words));
   G_TRY(g->alloc((void**)&g->qs.meta, sizeof(QueueMeta) * Q));
   G_TRY(g->alloc((void**)&g->qs.slots, sizeof(unsigned long long) * ((size_t)Q << cap_log2)));
   G_TRY(g->alloc((void**)&g->cq.meta, sizeof(QueueMeta) * Qc));
@@ -250,7 +252,6 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   G_TRY(g->alloc((void**)&g->ctl, sizeof(Control)));
   G_TRY(g->alloc((void**)&g->status_dev, sizeof(int32_t)));
   G_TRY(g->alloc((void**)&g->scratch, 2 * sizeof(unsigned long long)));
-  G_CUDA(cudaMemsetAsync(g->bitmap, 0, sizeof(unsigned) * (size_t)words, s));
   G_CUDA(cudaMemsetAsync(g->qs.meta, 0, sizeof(QueueMeta) * Q, s));
   G_CUDA(cudaMemsetAsync(g->qs.slots, 0, sizeof(unsigned long long) * ((size_t)Q << cap_log2), s));
   G_CUDA(cudaMemsetAsync(g->cq.meta, 0, sizeof(QueueMeta) * Qc, s));
@@ -282,7 +283,6 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.row_ptr = g->row_ptr;
   a.adj = g->adj;
   a.label = g->label;
-  a.bitmap = g->bitmap;
   a.qs = g->qs;
   a.cq = g->cq;
   a.hub_chunk0 = g->hub_chunk0;
@@ -295,6 +295,8 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.src = src;
   a.batch_items = g->tune.batch_items;
   a.queues_per_cta = g->tune.queues_per_cta;
+  a.share_div = g->tune.share_div;
+  a.chunk_batch = g->tune.chunk_batch;
   a.hub_degree = g->tune.hub_degree;
   a.chunk_edges = g->tune.chunk_edges;
   a.spin_limit = g->tune.spin_limit;
@@ -345,6 +347,7 @@ int bfq_get_stats(bfq_graph_t g, bfq_stats* out) {
   out->enqueued = (int64_t)c.ctr[kCtrEnq];
   out->steals = (int64_t)c.ctr[kCtrSteal];
   out->hub_chunks = (int64_t)c.ctr[kCtrChunk];
+  out->idle_polls = (int64_t)c.ctr[kCtrIdle];
   out->m_reached = (int64_t)red[0];
   out->reached = (int64_t)red[1];
   out->V = g->V;

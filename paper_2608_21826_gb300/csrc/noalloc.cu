@@ -35,7 +35,7 @@ void* g_scratch_dev[kNoAllocMaxDevices] = {};
 
 // Byte offsets of the per-call working set inside the scratch array.
 struct Layout {
-  size_t ctl, bad, qmeta, qslots, cmeta, cslots, bitmap, label, total;
+  size_t ctl, bad, qmeta, qslots, cmeta, cslots, label, total;
   int cap_log2;
 };
 
@@ -54,13 +54,12 @@ Layout layout_for(int V) {
   L.qslots = o; o = align_up(o + sizeof(unsigned long long) * ((size_t)kNoAllocQueues << l), 256);
   L.cmeta = o;  o = align_up(o + sizeof(QueueMeta), 256);
   L.cslots = o; o = align_up(o + sizeof(unsigned long long) * 256, 256);
-  L.bitmap = o; o = align_up(o + sizeof(unsigned) * (((size_t)V + 31) / 32), 256);
   L.label = o;  o = align_up(o + sizeof(long long) * (size_t)V, 256);
   L.total = o;
   return L;
 }
 
-// Zero the queues, bitmap and control block of this call's working set (the
+// Zero the queues and control block of this call's working set (the
 // array keeps whatever the previous call left), and check the CSR.
 __global__ void noalloc_prepare_kernel(unsigned char* base, Layout L, const int* row_ptr,
                                        const int* adj, int V, long long E) {
@@ -89,10 +88,9 @@ __global__ void noalloc_init_kernel(SsspArgs a, const int* bad) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   for (long long v = tid; v < a.V; v += nth)
-    a.label[v] = (ok && v == a.src) ? 0LL : kInfLabel;
+    a.label[v] = (ok && v == a.src) ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
   if (tid == 0) {
     if (ok) {
-      a.bitmap[a.src >> 5] = 1u << (a.src & 31);
       a.qs.slots[0] = (1ull << 32) | (unsigned)a.src;   // lap 0, full, at ticket 0
       a.qs.meta[0].tail = 1;
       a.qs.meta[0].count = 1;
@@ -101,16 +99,6 @@ __global__ void noalloc_init_kernel(SsspArgs a, const int* bad) {
     a.ctl->status = 0;
     a.ctl->stop = 0;
   }
-}
-
-__global__ void noalloc_finalize_kernel(const Control* ctl, const int* bad, int32_t* status_dev) {
-  const int st = ctl->status;
-  int code = BFQ_OK;
-  if (*bad) code = BFQ_ERR_INVALID;
-  else if (st & (kStTimeout | kStQueue)) code = BFQ_ERR_TIMEOUT;
-  else if (st & kStNegCycle) code = BFQ_NEG_CYCLE;
-  else if (st & kStRange) code = BFQ_RANGE;
-  *status_dev = code;
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -180,7 +168,6 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   a.row_ptr = row_ptr;
   a.adj = (const int2*)adj;
   a.label = (long long*)(base + L.label);
-  a.bitmap = (unsigned*)(base + L.bitmap);
   a.qs = QueueSet{(QueueMeta*)(base + L.qmeta), (unsigned long long*)(base + L.qslots),
                   kNoAllocQueues, L.cap_log2};
   a.cq = QueueSet{(QueueMeta*)(base + L.cmeta), (unsigned long long*)(base + L.cslots), 1, 8};
@@ -194,6 +181,8 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   a.src = src;
   a.batch_items = 32;
   a.queues_per_cta = 1;
+  a.share_div = 2;
+  a.chunk_batch = 4;
   a.hub_degree = 0x7fffffff;
   a.chunk_edges = 256;
   a.spin_limit = 1LL << 22;
@@ -206,7 +195,6 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   noalloc_init_kernel<<<init.grid, init.block, 0, s>>>(a, bad);
   BFQ_CUDA_TRY(cudaGetLastError());
   BFQ_CUDA_TRY(launch_sssp_persistent_only(a, run, s));
-  noalloc_finalize_kernel<<<1, 1, 0, s>>>(a.ctl, bad, status_dev);
-  BFQ_CUDA_TRY(cudaGetLastError());
+  BFQ_CUDA_TRY(launch_sssp_epilogue(a, init, status_dev, bad, s));
   return BFQ_OK;
 }

@@ -114,80 +114,211 @@ struct WarpCounters {
   unsigned long long deq = 0, rel = 0, upd = 0, enq = 0, steal = 0, chunk = 0, idle = 0;
 };
 
+// Warp-collective enqueue of up to U items per lane (group k of lane L is
+// queued when act[k]); ranks run group by group.  Items go to sub-queues of
+// qs starting at `home`, moving on while a sub-queue is full.  Returns the
+// number placed (lowest ranks first) or -1 if a ticket wait ran out.
+template <int U>
+__device__ __forceinline__ int enqueue_warp_multi(const QueueSet& qs, int home, const bool* act,
+                                                  const unsigned* item, int lane,
+                                                  long long spin_limit, long long max_tries) {
+  int rank[U];
+  int k = 0;
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    const unsigned m = __ballot_sync(kFullMask, act[g]);
+    rank[g] = k + __popc(m & ((1u << lane) - 1u));
+    k += __popc(m);
+  }
+  if (k == 0) return 0;
+  const int cap = 1 << qs.cap_log2;
+  int done = 0;
+  int q = home;
+  for (long long tries = 0; done < k && tries < max_tries; ++tries) {
+    unsigned long long pos = 0;
+    int got = 0;
+    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos);
+    got = __shfl_sync(kFullMask, got, 0);
+    if (got) {
+      pos = __shfl_sync(kFullMask, pos, 0);
+      bool ok = true;
+      unsigned long long* qslots = qs.slots + ((size_t)q << qs.cap_log2);
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        const int r = rank[g] - done;
+        if (act[g] && r >= 0 && r < got)
+          ok = wq_put(qslots, qs.cap_log2, pos + r, item[g], spin_limit) && ok;
+      }
+      if (__any_sync(kFullMask, !ok)) return -1;
+      done += got;
+    }
+    q = (q + 1 == qs.Q) ? 0 : q + 1;
+  }
+  return done;
+}
+
+constexpr int kChildBuf = 256;   // claimed children buffered per warp
+
+// Publish `count` items from the warp's buffer to the sub-queues of qs,
+// starting at `home`: one broker reservation (and one tail ticket range) per
+// sub-queue visited, every lane writing a share of the slots.  Returns false
+// if no room was found within the bounds or a ticket wait ran out.
+__device__ __forceinline__ bool enqueue_buffer(const QueueSet& qs, int home,
+                                               const unsigned* buf, int count, int lane,
+                                               long long spin_limit, long long max_tries) {
+  const int cap = 1 << qs.cap_log2;
+  int done = 0;
+  int q = home;
+  for (long long tries = 0; done < count && tries < max_tries; ++tries) {
+    unsigned long long pos = 0;
+    int got = 0;
+    if (lane == 0) got = wq_reserve(qs.meta + q, count - done, false, cap, &pos);
+    got = __shfl_sync(kFullMask, got, 0);
+    if (got) {
+      pos = __shfl_sync(kFullMask, pos, 0);
+      unsigned long long* qslots = qs.slots + ((size_t)q << qs.cap_log2);
+      bool ok = true;
+      for (int i = lane; i < got; i += 32)
+        ok = wq_put(qslots, qs.cap_log2, pos + i, buf[done + i], spin_limit) && ok;
+      if (__any_sync(kFullMask, !ok)) return false;
+      done += got;
+    }
+    q = (q + 1 == qs.Q) ? 0 : q + 1;
+  }
+  return done == count;
+}
+
+// Count the buffered children as in flight (before any becomes visible),
+// then publish them.
+__device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsigned* buf,
+                                               int& nbuf, int lane, WarpCounters& wc) {
+  if (nbuf == 0) return true;
+  __syncwarp();                         // buffer writes visible to all lanes
+  if (lane == 0) {
+    red_add_relaxed_s32(&a.ctl->inflight, nbuf);
+    wc.enq += nbuf;
+  }
+  __syncwarp();
+  const bool ok = enqueue_buffer(a.qs, home, buf, nbuf, lane, a.spin_limit, 4LL * a.qs.Q + 64);
+  __syncwarp();                         // buffer free for reuse
+  if (!ok && lane == 0) atomicOr(&a.ctl->status, kStQueue);
+  nbuf = 0;
+  return ok;
+}
+
+// Lower label[v] to `key` unless it is already at least as small; on success
+// set the in-queue flag in the same compare-and-swap.  Returns 0 (no
+// change), 1 (lowered, flag was already set) or 2 (lowered and this caller
+// must enqueue v).
+__device__ __forceinline__ int lower_label(long long* label_v, long long key, long long seen) {
+  long long old = seen;
+  while (key < label_key(old)) {
+    const long long prev = (long long)atomicCAS((unsigned long long*)label_v,
+                                                (unsigned long long)old,
+                                                (unsigned long long)(key | kQueuedBit));
+    if (prev == old) return (old & kQueuedBit) ? 1 : 2;
+    old = prev;
+  }
+  return 0;
+}
+
 // Relax the merged edge lists of the items held by lanes [0, n): lane j owns
 // edges [beg_j, beg_j + deg_j) of a tail whose label is lab_j.  Edges are
-// walked lane-contiguously, 32 per step.  Returns false on a timeout.
+// walked lane-contiguously, U groups of 32 per step so that the loads of
+// the groups overlap.  Returns false on a timeout.
+// Claimed children are appended to the warp's buffer `buf` (nbuf items,
+// capacity kChildBuf) and published in bulk by flush_children.
+template <int U>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
                                              long long lab, int lane, int home,
-                                             WarpCounters& wc) {
+                                             WarpCounters& wc, unsigned* buf, int& nbuf) {
   int total = 0;
   const int excl = warp_excl_scan(deg, lane, &total);
   wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
   const unsigned V = (unsigned)a.V;
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    const int j = owner_lane(excl, t, n);
-    const int ex_j = __shfl_sync(kFullMask, excl, j);
-    const int beg_j = __shfl_sync(kFullMask, beg, j);
-    const long long lab_j = __shfl_sync(kFullMask, lab, j);
-    bool want_enq = false;
-    unsigned v = 0;
-    if (t < total) {
-      const int2 cw = __ldg(&a.adj[beg_j + (t - ex_j)]);
-      v = (unsigned)cw.x;
-      const long long nd = (long long)label_dist(lab_j) + (long long)cw.y;
-      if (nd < (long long)kInf32) {
-        if (nd <= -2147483648LL) {
-          raise_status(a.ctl, kStRange);
-        } else {
-          const unsigned nh = label_hops(lab_j) + 1u;
-          const long long key = pack_label((int)nd, nh);
-          if (key < ld_relaxed_s64(&a.label[v])) {
-            const long long old = atomicMin((long long*)&a.label[v], key);
-            if (key < old) {
-              ++wc.upd;
-              if (nh >= V) {
-                raise_status(a.ctl, kStNegCycle);
-              } else {
-                // label write -> fence -> in-queue bit; pairs with the
-                // consumer's bit clear -> fence -> label read
-                fence_acq_rel_gpu();
-                const unsigned bit = 1u << (v & 31u);
-                const unsigned ob = atomicOr(&a.bitmap[v >> 5], bit);
-                want_enq = (ob & bit) == 0u;
-              }
-            }
-          }
+  for (int base = 0; base < total; base += 32 * U) {
+    int2 cw[U];
+    long long lab_t[U];
+    bool act[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      act[g] = false;
+      cw[g] = make_int2(0, 0);
+      lab_t[g] = 0;
+      if (base + 32 * g < total) {          // warp-uniform
+        const int t = base + 32 * g + lane;
+        const int j = owner_lane(excl, t, n);
+        const int ex_j = __shfl_sync(kFullMask, excl, j);
+        const int beg_j = __shfl_sync(kFullMask, beg, j);
+        lab_t[g] = __shfl_sync(kFullMask, lab, j);
+        if (t < total) {
+          act[g] = true;
+          cw[g] = __ldg(&a.adj[beg_j + (t - ex_j)]);
         }
       }
     }
-    const unsigned m = __ballot_sync(kFullMask, want_enq);
-    if (m) {
-      // the new items are counted before any of them becomes visible
-      if (lane == 0) {
-        atomicAdd(&a.ctl->inflight, __popc(m));
-        wc.enq += __popc(m);
+    long long key[U], cur[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      key[g] = 0;
+      cur[g] = 0;
+      if (act[g]) {
+        const long long nd = (long long)label_dist(lab_t[g]) + (long long)cw[g].y;
+        if (nd >= (long long)kInf32) {
+          act[g] = false;
+        } else if (nd <= -2147483648LL) {
+          raise_status(a.ctl, kStRange);
+          act[g] = false;
+        } else {
+          key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
+          cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
+        }
       }
-      __syncwarp();
-      const int placed = enqueue_warp(a.qs, home, want_enq, v, lane, a.spin_limit,
-                                      4LL * a.qs.Q + 64);
-      if (placed != __popc(m)) {
-        if (lane == 0 && placed >= 0) atomicOr(&a.ctl->status, kStQueue);
-        return false;
+    }
+    bool enq[U];
+    unsigned item[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      enq[g] = false;
+      item[g] = (unsigned)cw[g].x;
+      if (act[g]) {
+        const int r = lower_label(&a.label[cw[g].x], key[g], cur[g]);
+        if (r) {
+          ++wc.upd;
+          if (label_hops(key[g]) >= V) raise_status(a.ctl, kStNegCycle);
+          else enq[g] = (r == 2);
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      const unsigned m = __ballot_sync(kFullMask, enq[g]);
+      if (m) {
+        if (nbuf + __popc(m) > kChildBuf) {
+          if (!flush_children(a, home, buf, nbuf, lane, wc)) return false;
+        }
+        if (enq[g]) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = item[g];
+        nbuf += __popc(m);
       }
     }
   }
   return true;
 }
 
+#ifndef BFQ_EDGE_GROUPS
+#define BFQ_EDGE_GROUPS 4
+#endif
+constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per warp step
+
 // Publish the hub chunks [c0_j, c0_j + nch_j) of the lanes with nch > 0 to
 // the chunk sub-queues.  Chunks that find no room are relaxed right here.
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
-                                            int home, int chome, WarpCounters& wc) {
+                                            int home, int chome, WarpCounters& wc,
+                                            unsigned* buf, int& nbuf) {
   int K = 0;
   const int excl = warp_excl_scan(nch, lane, &K);
   if (K == 0) return true;
-  if (lane == 0) atomicAdd(&a.ctl->inflight, K);
+  if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, K);
   __syncwarp();
   for (int base = 0; base < K; base += 32) {
     const int t = base + lane;
@@ -212,61 +343,77 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
         const int4 ct = a.chunk_tab[cid];
         beg = ct.y;
         deg = ct.z - ct.y;
-        lab = ld_relaxed_s64(&a.label[ct.x]);
+        lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged(a, 1, beg, deg, lab, lane, home, wc)) return false;
-      __syncwarp();
-      if (lane == 0) atom_add_release_s32(&a.ctl->inflight, -1);
+      if (!relax_merged<kGroups>(a, 1, beg, deg, lab, lane, home, wc, buf, nbuf) ||
+          !flush_children(a, home, buf, nbuf, lane, wc))
+        return false;
+      if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -1);
     }
   }
   return true;
 }
 
-// Dequeue from sub-queue q of qs, taking a share of its items proportional
-// to the warps that serve it.
-__device__ __forceinline__ int dequeue_share(const QueueSet& qs, int q, int max_items,
-                                             int share, int lane, unsigned* item,
-                                             long long spin_limit) {
-  int cnt = 0;
-  if (lane == 0) cnt = ld_relaxed_s32(&qs.meta[q].count);
-  cnt = __shfl_sync(kFullMask, cnt, 0);
-  if (cnt <= 0) return 0;
-  const int want = min(max_items, max(1, (cnt + share - 1) / share));
-  return wq_dequeue_warp(qs, q, want, lane, item, spin_limit);
+__device__ __forceinline__ int share_of(int cnt, int max_items, int share) {
+  return min(max_items, max(1, (cnt + share - 1) / share));
 }
 
-__global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
+#ifndef BFQ_MIN_CTAS_PER_SM
+#define BFQ_MIN_CTAS_PER_SM 4
+#endif
+__global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_kernel(SsspArgs a) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int home = (blockIdx.x * a.queues_per_cta + wid % a.queues_per_cta) % a.qs.Q;
   const int chome = blockIdx.x % a.cq.Q;
-  const int share = max(1, nwarps / a.queues_per_cta);
+  const int share = a.share_div > 0 ? a.share_div : max(1, nwarps / a.queues_per_cta);
   WarpCounters wc;
   const unsigned long long t_start = globaltimer_ns();
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
   bool timed_out = false;
 
+  __shared__ unsigned s_children[kBlock / 32][kChildBuf];
+  unsigned* buf = s_children[wid];
+  int nbuf = 0;
   for (;;) {
     unsigned item = 0;
-    // hub chunks first (they sit on the critical path), then the own
-    // vertex sub-queue, then stealing
-    bool is_chunk = true;
-    int got = dequeue_share(a.cq, chome, 1, 1, lane, &item, a.spin_limit);
-    if (got == 0) {
+    int got = 0;
+    bool is_chunk = false;
+    // hub chunks first (they sit on the critical path), then the own vertex
+    // sub-queue, then stealing; both home counts are read in one step
+    int c = 0;
+    if (lane == 0) c = ld_relaxed_s32(&a.cq.meta[chome].count);
+    else if (lane == 1) c = ld_relaxed_s32(&a.qs.meta[home].count);
+    const int c_chunk = __shfl_sync(kFullMask, c, 0);
+    const int c_vert = __shfl_sync(kFullMask, c, 1);
+    if (c_chunk > 0) {
+      is_chunk = true;
+      got = wq_dequeue_warp(a.cq, chome, a.chunk_batch, lane, &item, a.spin_limit, c_chunk);
+    }
+    if (got == 0 && c_vert > 0) {
       is_chunk = false;
-      got = dequeue_share(a.qs, home, a.batch_items, share, lane, &item, a.spin_limit);
+      got = wq_dequeue_warp(a.qs, home, share_of(c_vert, a.batch_items, share), lane, &item,
+                            a.spin_limit, c_vert);
     }
     if (got == 0) {
       rng = rng * 1664525u + 1013904223u;
       int q = probe_queues(a.cq, (int)(rng % (unsigned)a.cq.Q), chome, lane);
       if (q >= 0) {
         is_chunk = true;
-        got = dequeue_share(a.cq, q, 1, 1, lane, &item, a.spin_limit);
+        got = wq_dequeue_warp(a.cq, q, a.chunk_batch, lane, &item, a.spin_limit);
       } else {
         q = probe_queues(a.qs, (int)((rng >> 7) % (unsigned)a.qs.Q), home, lane);
-        if (q >= 0) got = dequeue_share(a.qs, q, a.batch_items, share, lane, &item, a.spin_limit);
+        if (q >= 0) {
+          is_chunk = false;
+          int cq_cnt = 0;
+          if (lane == 0) cq_cnt = ld_relaxed_s32(&a.qs.meta[q].count);
+          cq_cnt = __shfl_sync(kFullMask, cq_cnt, 0);
+          if (cq_cnt > 0)
+            got = wq_dequeue_warp(a.qs, q, share_of(cq_cnt, a.batch_items, share), lane, &item,
+                                  a.spin_limit, cq_cnt);
+        }
       }
       if (got > 0) ++wc.steal;
     }
@@ -274,7 +421,7 @@ __global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
     if (got == 0) {
       int done = 0;
       if (lane == 0)
-        done = (ld_acquire_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
+        done = (ld_relaxed_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
       if (__shfl_sync(kFullMask, done, 0)) break;
       ++wc.idle;
       __nanosleep(min(32u << min(idle, 6), 2048u));
@@ -297,13 +444,13 @@ __global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
         const int4 ct = a.chunk_tab[item];
         beg = ct.y;
         deg = ct.z - ct.y;
-        lab = ld_relaxed_s64(&a.label[ct.x]);
+        lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       } else {
         const unsigned u = item;
-        // clear the in-queue bit, then read the label (see relax_merged)
-        atomicAnd(&a.bitmap[u >> 5], ~(1u << (u & 31u)));
-        fence_acq_rel_gpu();
-        lab = ld_relaxed_s64(&a.label[u]);
+        // clear the in-queue flag and read the label in one atomic: any
+        // later improvement sees the flag clear and queues u again
+        lab = label_key((long long)atomicAnd((unsigned long long*)&a.label[u],
+                                             ~(unsigned long long)kQueuedBit));
         beg = __ldg(&a.row_ptr[u]);
         deg = __ldg(&a.row_ptr[u + 1]) - beg;
         if (deg > a.hub_degree) {
@@ -314,18 +461,22 @@ __global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks(a, nch, c0, lane, home, chome, wc)) { timed_out = true; break; }
+      if (!push_chunks(a, nch, c0, lane, home, chome, wc, buf, nbuf)) {
+        timed_out = true;
+        break;
+      }
     }
-    if (!relax_merged(a, got, beg, deg, lab, lane, home, wc)) {
+    if (!relax_merged<kGroups>(a, got, beg, deg, lab, lane, home, wc, buf, nbuf) ||
+        !flush_children(a, home, buf, nbuf, lane, wc)) {
       timed_out = true;
       break;
     }
-    // retire the batch: the warp's label writes and enqueues are ordered
-    // before the decrement (syncwarp, then a release add)
-    __syncwarp();
+    // retire the batch.  Its children were counted by this lane earlier, on
+    // the same counter, so coherence orders this decrement after them; the
+    // labels are read by the epilogue kernel, after this kernel has ended.
     int stop = 0;
     if (lane == 0) {
-      atom_add_release_s32(&a.ctl->inflight, -got);
+      red_add_relaxed_s32(&a.ctl->inflight, -got);
       stop = ld_relaxed_s32(&a.ctl->stop);
     }
     if (__shfl_sync(kFullMask, stop, 0)) break;
@@ -342,36 +493,46 @@ __global__ void __launch_bounds__(kBlock) sssp_persistent_kernel(SsspArgs a) {
     if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], wc.chunk);
     if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], wc.idle);
   }
-  __syncthreads();
+}
 
-  // epilogue: unpack this CTA's slice of the labels.  Every warp left its
-  // loop after seeing the in-flight count at zero (acquire), so every label
-  // write has happened; after an early stop the results are unspecified.
-  const long long per = ((long long)a.V + gridDim.x - 1) / gridDim.x;
-  const long long lo = per * blockIdx.x;
-  const long long hi = min((long long)a.V, lo + per);
-  for (long long v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-    const long long l = ld_relaxed_s64(&a.label[v]);
-    a.dist[v] = label_dist(l);
-    if (a.hops) a.hops[v] = (int)label_hops(l);
+// Epilogue: unpack the labels into dist / hops (pred to -1 for the optional
+// predecessor pass), and turn the status bits into the run's status code,
+// also kept for the next run's init.  Runs after the persistent kernel, so
+// every label write is visible; after an early stop the results are
+// unspecified.
+__global__ void sssp_epilogue_kernel(SsspArgs a, int32_t* status_dev, const int* bad) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < a.V; v += nth) {
+    const long long l = a.label[v];
+    const int d = label_dist(l);
+    a.dist[v] = d;
+    if (a.hops) a.hops[v] = (d == kInf32) ? -1 : (int)label_hops(l);
     if (a.pred) a.pred[v] = -1;
+  }
+  if (tid == 0) {
+    const int st = a.ctl->status;
+    int code = BFQ_OK;
+    if (bad && *bad) code = BFQ_ERR_INVALID;
+    else if (st & (kStTimeout | kStQueue)) code = BFQ_ERR_TIMEOUT;
+    else if (st & kStNegCycle) code = BFQ_NEG_CYCLE;
+    else if (st & kStRange) code = BFQ_RANGE;
+    a.ctl->last_status = code;
+    if (status_dev) *status_dev = code;
   }
 }
 
-// Labels start at (INT32_MAX, 0xffffffff), the source at (0, 0); the source
-// is queued in vertex sub-queue 0.  If the previous run ended early
-// (last_status != 0) the bitmap and all sub-queues are reset first; a clean
-// run leaves every sub-queue empty and every bit clear.
+// Labels start at (INT32_MAX, -) and not queued, the source at (0, 0) and
+// queued in vertex sub-queue 0.  If the previous run ended early
+// (last_status != 0) all sub-queues are reset first; a clean run leaves every
+// sub-queue empty and every in-queue flag clear.
 __global__ void sssp_init_kernel(SsspArgs a) {
   const bool dirty = a.ctl->last_status != 0;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
-  for (long long v = tid; v < a.V; v += nth) a.label[v] = (v == a.src) ? 0LL : kInfLabel;
-  const long long sw = a.src >> 5;
-  const unsigned sbit = 1u << (a.src & 31);
+  for (long long v = tid; v < a.V; v += nth)
+    a.label[v] = (v == a.src) ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
   if (dirty) {
-    const long long words = ((long long)a.V + 31) / 32;
-    for (long long i = tid; i < words; i += nth) a.bitmap[i] = (i == sw) ? sbit : 0u;
     const long long nslots = (long long)a.qs.Q << a.qs.cap_log2;
     for (long long i = tid; i < nslots; i += nth)
       a.qs.slots[i] = (i == 0) ? ((1ull << 32) | (unsigned)a.src) : 0ull;
@@ -388,7 +549,6 @@ __global__ void sssp_init_kernel(SsspArgs a) {
       a.cq.meta[q].tail = 0;
     }
   } else if (tid == 0) {
-    a.bitmap[sw] = sbit;
     QueueMeta* m = a.qs.meta;
     const unsigned long long p = m->tail;
     const unsigned lap = (unsigned)(p >> a.qs.cap_log2);
@@ -405,17 +565,6 @@ __global__ void sssp_init_kernel(SsspArgs a) {
   }
 }
 
-// Status code of the run, also kept for the next run's init.
-__global__ void sssp_finalize_kernel(Control* ctl, int32_t* status_dev) {
-  const int st = ctl->status;
-  int code = BFQ_OK;
-  if (st & (kStTimeout | kStQueue)) code = BFQ_ERR_TIMEOUT;
-  else if (st & kStNegCycle) code = BFQ_NEG_CYCLE;
-  else if (st & kStRange) code = BFQ_RANGE;
-  ctl->last_status = code;
-  if (status_dev) *status_dev = code;
-}
-
 // Predecessor post-pass: for each reached u and edge (u, v, w) with
 // dist[u] + w == dist[v] and hops[u] + 1 == hops[v], pred[v] = u.  Any such u
 // is valid; following pred strictly lowers hops, so the tree is acyclic.
@@ -427,14 +576,14 @@ __global__ void sssp_pred_kernel(const int* __restrict__ row_ptr, const int2* __
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long u = warp; u < V; u += nw) {
-    const long long lu = label[u];
+    const long long lu = label_key(label[u]);
     if (label_dist(lu) == kInf32) continue;
     const int b = row_ptr[u], e = row_ptr[u + 1];
     for (int i = b + lane; i < e; i += 32) {
       const int2 cw = adj[i];
       const long long nd = (long long)label_dist(lu) + cw.y;
       if (nd >= kInf32) continue;
-      const long long lv = label[cw.x];
+      const long long lv = label_key(label[cw.x]);
       if (label_dist(lv) == (int)nd && label_hops(lv) == label_hops(lu) + 1u) pred[cw.x] = (int)u;
     }
   }
@@ -506,7 +655,7 @@ cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape r
   if (ev0) cudaEventRecord(ev0, s);
   sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
   if (ev1) cudaEventRecord(ev1, s);
-  sssp_finalize_kernel<<<1, 1, 0, s>>>(a.ctl, status_dev);
+  sssp_epilogue_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a, status_dev, nullptr);
   if (a.pred)
     sssp_pred_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a.row_ptr, a.adj, a.label, a.V,
                                                                  a.pred, a.ctl);
@@ -541,6 +690,12 @@ cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s) {
 cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
                                         cudaStream_t s) {
   sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sssp_epilogue(const SsspArgs& a, LaunchShape shape, int32_t* status_dev,
+                                 const int* bad, cudaStream_t s) {
+  sssp_epilogue_kernel<<<shape.grid, shape.block, 0, s>>>(a, status_dev, bad);
   return cudaGetLastError();
 }
 
