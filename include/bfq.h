@@ -187,6 +187,45 @@ int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
                      int64_t E, int32_t src, int32_t* dist, int32_t* hops,
                      int32_t* status_dev, void* stream);
 
+/* Pick the run-time parameters (share_div, chunk_batch, batch_items) that
+ * make the queries from srcs[0..n) (host array) fastest on g, keep them on
+ * the handle and copy them to *out (nullable).  Tries a fixed grid of
+ * candidates, timing each with CUDA events; allocates one int32[V] scratch
+ * array for the duration.  Synchronises `stream`. */
+int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
+
+/* ---- batched queries: many sources over many resident graphs in one
+ * persistent launch, replayed from a captured CUDA graph ------------------ */
+/* graphs: host array of ngraphs handles (they must outlive the batch).
+ * max_queries <= 4096 queries per call; max_total_vertices bounds the sum of
+ * V over one call's queries (<= 0: max V x max_queries) and sizes the label
+ * pool and sub-queues.  tune may be NULL. */
+int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
+                     int32_t max_queries, int64_t max_total_vertices,
+                     const bfq_tune* tune);
+int bfq_batch_destroy(bfq_batch_t b);
+int64_t bfq_batch_device_bytes(bfq_batch_t b);
+/* Run nq queries (graph_id[q], src[q]: host arrays) in one launch.  dist and
+ * hops are host arrays of nq device pointers (int32[V_q] each; hops may be
+ * NULL or hold NULLs).  status (host, int32[nq]) receives each query's
+ * status (BFQ_OK, BFQ_NEG_CYCLE, BFQ_RANGE, BFQ_ERR_TIMEOUT).  A query with a
+ * negative cycle stops alone; the others finish.  Synchronises `stream`;
+ * returns BFQ_OK, BFQ_ERR_TIMEOUT if the launch ran out of time, or an
+ * argument error (nq > max_queries, vertices beyond max_total_vertices). */
+int bfq_sssp_batch(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
+                   const int32_t* src, int32_t* const* dist, int32_t* const* hops,
+                   int32_t* status, void* stream);
+/* Counters of the last batch launch (kernel_ms = whole captured run). */
+int bfq_batch_get_stats(bfq_batch_t b, bfq_stats* out);
+/* Set the run-time parameters (share_div, chunk_batch, batch_items,
+ * time_limit_ms; zero fields are left unchanged). */
+int bfq_batch_set_tune(bfq_batch_t b, const bfq_tune* t);
+/* Autotuner: runs the given query set under a grid of run-time parameters,
+ * keeps the fastest on the handle and copies it to *out (nullable). */
+int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
+                       const int32_t* src, int32_t* const* dist,
+                       int32_t* const* hops, bfq_tune* out, void* stream);
+
 /* ---- standalone Broker Queue (Sec. III-A, Algorithm 1; Sec. IV workloads) */
 /* A ring of `capacity` int32 items (rounded up to a power of two for the
  * warp variant), variant = BFQ_QUEUE_*. */

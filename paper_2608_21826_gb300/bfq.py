@@ -65,6 +65,16 @@ _SIGNATURES = {
     "bfq_sssp_async": ([_VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "bfq_get_stats": ([_VP, ctypes.POINTER(Stats)], ctypes.c_int),
     "bfq_sssp_noalloc": ([_VP, _VP, _I32, _I64, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "bfq_autotune": ([_VP, _VP, _I32, ctypes.POINTER(Tune), _VP], ctypes.c_int),
+    "bfq_batch_create": ([ctypes.POINTER(_VP), _VP, _I32, _I32, _I64, ctypes.POINTER(Tune)],
+                         ctypes.c_int),
+    "bfq_batch_destroy": ([_VP], ctypes.c_int),
+    "bfq_batch_device_bytes": ([_VP], _I64),
+    "bfq_sssp_batch": ([_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "bfq_batch_get_stats": ([_VP, ctypes.POINTER(Stats)], ctypes.c_int),
+    "bfq_batch_set_tune": ([_VP, ctypes.POINTER(Tune)], ctypes.c_int),
+    "bfq_batch_autotune": ([_VP, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(Tune), _VP],
+                           ctypes.c_int),
     "bfq_queue_create": ([ctypes.POINTER(_VP), _I64, _I32], ctypes.c_int),
     "bfq_queue_destroy": ([_VP], ctypes.c_int),
     "bfq_queue_reset": ([_VP, _VP], ctypes.c_int),
@@ -206,6 +216,75 @@ def bfq_sssp_noalloc(row_ptr, adj, V: int, E: int, src: int, dist, hops=None, st
     return _check(lib().bfq_sssp_noalloc(_ptr(row_ptr), _ptr(adj), int(V), int(E), int(src),
                                          _ptr(dist), _ptr(hops), _ptr(status_dev),
                                          _stream(stream)))
+
+
+def bfq_autotune(g, srcs, stream=None) -> Tune:
+    """Pick the fastest run-time parameters for these sources; kept on g."""
+    a = np.ascontiguousarray(srcs, dtype=np.int32)
+    t = Tune()
+    _check(lib().bfq_autotune(g, _ptr(a), len(a), ctypes.byref(t), _stream(stream)))
+    return t
+
+
+# ---- batched queries -------------------------------------------------------------
+
+def _ptr_array(xs, n):
+    arr = (_VP * max(1, n))()
+    for i in range(n):
+        x = xs[i] if xs is not None else None
+        arr[i] = None if x is None else (x.data_ptr() if hasattr(x, "data_ptr") else int(x))
+    return arr
+
+
+def bfq_batch_create(graphs, max_queries: int, max_total_vertices: int = 0,
+                     tune: Tune | None = None):
+    hs = (_VP * len(graphs))(*[g.value if isinstance(g, _VP) else g for g in graphs])
+    h = _VP()
+    _check(lib().bfq_batch_create(ctypes.byref(h), hs, len(graphs), int(max_queries),
+                                  int(max_total_vertices), ctypes.byref(tune) if tune else None))
+    return h
+
+
+def bfq_batch_destroy(b) -> None:
+    _check(lib().bfq_batch_destroy(b))
+
+
+def bfq_batch_device_bytes(b) -> int:
+    return int(lib().bfq_batch_device_bytes(b))
+
+
+def bfq_sssp_batch(b, graph_id, src, dist, hops=None, stream=None):
+    """Run len(src) queries in one launch; dist/hops are lists of CUDA
+    tensors.  Returns (rc, statuses)."""
+    gid = np.ascontiguousarray(graph_id, dtype=np.int32)
+    sr = np.ascontiguousarray(src, dtype=np.int32)
+    n = len(sr)
+    st = np.zeros(max(1, n), dtype=np.int32)
+    rc = _check(lib().bfq_sssp_batch(b, n, _ptr(gid), _ptr(sr), _ptr_array(dist, n),
+                                     _ptr_array(hops, n) if hops is not None else None,
+                                     _ptr(st), _stream(stream)))
+    return rc, st[:n]
+
+
+def bfq_batch_get_stats(b) -> dict:
+    s = Stats()
+    _check(lib().bfq_batch_get_stats(b, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+
+
+def bfq_batch_set_tune(b, tune: Tune) -> None:
+    _check(lib().bfq_batch_set_tune(b, ctypes.byref(tune)))
+
+
+def bfq_batch_autotune(b, graph_id, src, dist, hops=None, stream=None) -> Tune:
+    gid = np.ascontiguousarray(graph_id, dtype=np.int32)
+    sr = np.ascontiguousarray(src, dtype=np.int32)
+    n = len(sr)
+    t = Tune()
+    _check(lib().bfq_batch_autotune(b, n, _ptr(gid), _ptr(sr), _ptr_array(dist, n),
+                                    _ptr_array(hops, n) if hops is not None else None,
+                                    ctypes.byref(t), _stream(stream)))
+    return t
 
 
 # ---- standalone queue ----------------------------------------------------------

@@ -79,6 +79,28 @@ struct bfq_graph {
   }
 };
 
+namespace bfq {
+struct GraphView {
+  const int* row_ptr;
+  const int2* adj;
+  const int* hub_chunk0;
+  const int4* chunk_tab;
+  int V, n_chunks, hub_degree, chunk_edges;
+};
+int graph_view(bfq_graph_t g, GraphView* out) {
+  if (!g || !out) return BFQ_ERR_INVALID;
+  out->row_ptr = g->row_ptr;
+  out->adj = g->adj;
+  out->hub_chunk0 = g->hub_chunk0;
+  out->chunk_tab = g->chunk_tab;
+  out->V = g->V;
+  out->n_chunks = g->n_chunks;
+  out->hub_degree = g->tune.hub_degree;
+  out->chunk_edges = g->tune.chunk_edges;
+  return BFQ_OK;
+}
+}  // namespace bfq
+
 extern "C" {
 
 const char* bfq_last_error(void) { return g_last_error.c_str(); }
@@ -360,6 +382,48 @@ int bfq_get_stats(bfq_graph_t g, bfq_stats* out) {
   if (cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
   cudaGetLastError();   // no run yet: events never recorded
   return BFQ_OK;
+}
+
+int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream) {
+  if (!g || !srcs || n < 1) return invalid("bfq_autotune: null argument or no sources");
+  for (int i = 0; i < n; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->V) return invalid("bfq_autotune: source out of range");
+  static const int kShare[] = {1, 2, 4, 8};
+  static const int kChunk[] = {2, 4, 8};
+  static const int kItems[] = {16, 32};
+  cudaStream_t s = (cudaStream_t)stream;
+  int* dist = nullptr;
+  BFQ_CUDA_TRY(cudaMalloc((void**)&dist, sizeof(int) * (size_t)g->V));
+  const bfq_tune keep = g->tune;
+  bfq_tune best_t = keep;
+  float best = -1.f;
+  int rc = BFQ_OK;
+  for (int si : kShare)
+    for (int ci : kChunk)
+      for (int ii : kItems) {
+        g->tune.share_div = si;
+        g->tune.chunk_batch = ci;
+        g->tune.batch_items = ii;
+        float total = 0.f;
+        for (int rep = 0; rep < 2 && rc == BFQ_OK; ++rep) {
+          for (int i = 0; i < n && rc == BFQ_OK; ++i) {
+            int st = bfq_sssp(g, srcs[i], dist, nullptr, nullptr, stream);
+            if (st < 0) rc = st;
+            float ms = 0.f;
+            if (rep == 1 && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) total += ms;
+          }
+        }
+        if (rc != BFQ_OK) break;
+        if (best < 0.f || total < best) {
+          best = total;
+          best_t = g->tune;
+        }
+      }
+  cudaStreamSynchronize(s);
+  cudaFree(dist);
+  g->tune = (rc == BFQ_OK) ? best_t : keep;
+  if (out && rc == BFQ_OK) *out = best_t;
+  return rc;
 }
 
 }  // extern "C"

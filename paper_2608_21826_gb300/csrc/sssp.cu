@@ -16,177 +16,11 @@
 //
 // Vertices of out-degree > hub_degree are split into chunks of chunk_edges
 // edges published to a second set of sub-queues, so many warps share a hub.
-#include "bfq_internal.h"
+#include "sssp_common.cuh"
 
 namespace bfq {
 
 namespace {
-
-constexpr int kBlock = 256;
-
-__device__ __forceinline__ void raise_status(Control* ctl, int bits) {
-  atomicOr(&ctl->status, bits);
-  st_relaxed_s32(&ctl->stop, 1);
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
-  return x;
-}
-
-// Exclusive prefix of `x` over the warp; *total receives the sum.
-__device__ __forceinline__ int warp_excl_scan(int x, int lane, int* total) {
-  int incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int n = __shfl_up_sync(kFullMask, incl, o);
-    if (lane >= o) incl += n;
-  }
-  *total = __shfl_sync(kFullMask, incl, 31);
-  return incl - x;
-}
-
-// For position t of a merged list, the owning lane: the largest j < n with
-// excl_j <= t (excl non-decreasing over lanes).
-__device__ __forceinline__ int owner_lane(int excl, int t, int n) {
-  int j = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int cand = j + step;
-    const int ex = __shfl_sync(kFullMask, excl, cand & 31);
-    if (cand < n && ex <= t) j = cand;
-  }
-  return j;
-}
-
-// Lanes probe up to 64 sub-queues starting at `start`; returns the fullest
-// non-empty one seen, or -1.
-__device__ __forceinline__ int probe_queues(const QueueSet& qs, int start, int skip, int lane) {
-  for (int r = 0; r < 2 && r * 32 < qs.Q; ++r) {
-    const int i = r * 32 + lane;
-    const int q = (start + i) % qs.Q;
-    const int c = (i < qs.Q && q != skip) ? ld_relaxed_s32(&qs.meta[q].count) : 0;
-    const int m = __reduce_max_sync(kFullMask, c);
-    if (m > 0) {
-      const unsigned who = __ballot_sync(kFullMask, c == m);
-      return __shfl_sync(kFullMask, q, __ffs(who) - 1);
-    }
-  }
-  return -1;
-}
-
-// Warp-collective enqueue of the lanes with `active` into the sub-queues of
-// qs, starting at `home` and moving on while a sub-queue is full, for at most
-// max_tries reservations.  Returns the number of items placed (the active
-// lanes of lowest rank), or -1 if a ticket wait ran out.
-__device__ __forceinline__ int enqueue_warp(const QueueSet& qs, int home, bool active,
-                                            unsigned item, int lane, long long spin_limit,
-                                            long long max_tries) {
-  const unsigned mask = __ballot_sync(kFullMask, active);
-  if (!mask) return 0;
-  const int k = __popc(mask);
-  const int rank = __popc(mask & ((1u << lane) - 1u));
-  const int cap = 1 << qs.cap_log2;
-  int done = 0;
-  int q = home;
-  for (long long tries = 0; done < k && tries < max_tries; ++tries) {
-    unsigned long long pos = 0;
-    int got = 0;
-    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos);
-    got = __shfl_sync(kFullMask, got, 0);
-    if (got) {
-      pos = __shfl_sync(kFullMask, pos, 0);
-      const int r = rank - done;
-      bool ok = true;
-      if (active && r >= 0 && r < got)
-        ok = wq_put(qs.slots + ((size_t)q << qs.cap_log2), qs.cap_log2, pos + r, item,
-                    spin_limit);
-      if (__any_sync(kFullMask, !ok)) return -1;
-      done += got;
-    }
-    q = (q + 1 == qs.Q) ? 0 : q + 1;
-  }
-  return done;
-}
-
-struct WarpCounters {
-  unsigned long long deq = 0, rel = 0, upd = 0, enq = 0, steal = 0, chunk = 0, idle = 0;
-};
-
-// Warp-collective enqueue of up to U items per lane (group k of lane L is
-// queued when act[k]); ranks run group by group.  Items go to sub-queues of
-// qs starting at `home`, moving on while a sub-queue is full.  Returns the
-// number placed (lowest ranks first) or -1 if a ticket wait ran out.
-template <int U>
-__device__ __forceinline__ int enqueue_warp_multi(const QueueSet& qs, int home, const bool* act,
-                                                  const unsigned* item, int lane,
-                                                  long long spin_limit, long long max_tries) {
-  int rank[U];
-  int k = 0;
-#pragma unroll
-  for (int g = 0; g < U; ++g) {
-    const unsigned m = __ballot_sync(kFullMask, act[g]);
-    rank[g] = k + __popc(m & ((1u << lane) - 1u));
-    k += __popc(m);
-  }
-  if (k == 0) return 0;
-  const int cap = 1 << qs.cap_log2;
-  int done = 0;
-  int q = home;
-  for (long long tries = 0; done < k && tries < max_tries; ++tries) {
-    unsigned long long pos = 0;
-    int got = 0;
-    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos);
-    got = __shfl_sync(kFullMask, got, 0);
-    if (got) {
-      pos = __shfl_sync(kFullMask, pos, 0);
-      bool ok = true;
-      unsigned long long* qslots = qs.slots + ((size_t)q << qs.cap_log2);
-#pragma unroll
-      for (int g = 0; g < U; ++g) {
-        const int r = rank[g] - done;
-        if (act[g] && r >= 0 && r < got)
-          ok = wq_put(qslots, qs.cap_log2, pos + r, item[g], spin_limit) && ok;
-      }
-      if (__any_sync(kFullMask, !ok)) return -1;
-      done += got;
-    }
-    q = (q + 1 == qs.Q) ? 0 : q + 1;
-  }
-  return done;
-}
-
-constexpr int kChildBuf = 256;   // claimed children buffered per warp
-
-// Publish `count` items from the warp's buffer to the sub-queues of qs,
-// starting at `home`: one broker reservation (and one tail ticket range) per
-// sub-queue visited, every lane writing a share of the slots.  Returns false
-// if no room was found within the bounds or a ticket wait ran out.
-__device__ __forceinline__ bool enqueue_buffer(const QueueSet& qs, int home,
-                                               const unsigned* buf, int count, int lane,
-                                               long long spin_limit, long long max_tries) {
-  const int cap = 1 << qs.cap_log2;
-  int done = 0;
-  int q = home;
-  for (long long tries = 0; done < count && tries < max_tries; ++tries) {
-    unsigned long long pos = 0;
-    int got = 0;
-    if (lane == 0) got = wq_reserve(qs.meta + q, count - done, false, cap, &pos);
-    got = __shfl_sync(kFullMask, got, 0);
-    if (got) {
-      pos = __shfl_sync(kFullMask, pos, 0);
-      unsigned long long* qslots = qs.slots + ((size_t)q << qs.cap_log2);
-      bool ok = true;
-      for (int i = lane; i < got; i += 32)
-        ok = wq_put(qslots, qs.cap_log2, pos + i, buf[done + i], spin_limit) && ok;
-      if (__any_sync(kFullMask, !ok)) return false;
-      done += got;
-    }
-    q = (q + 1 == qs.Q) ? 0 : q + 1;
-  }
-  return done == count;
-}
 
 // Count the buffered children as in flight (before any becomes visible),
 // then publish them.
@@ -204,22 +38,6 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
   if (!ok && lane == 0) atomicOr(&a.ctl->status, kStQueue);
   nbuf = 0;
   return ok;
-}
-
-// Lower label[v] to `key` unless it is already at least as small; on success
-// set the in-queue flag in the same compare-and-swap.  Returns 0 (no
-// change), 1 (lowered, flag was already set) or 2 (lowered and this caller
-// must enqueue v).
-__device__ __forceinline__ int lower_label(long long* label_v, long long key, long long seen) {
-  long long old = seen;
-  while (key < label_key(old)) {
-    const long long prev = (long long)atomicCAS((unsigned long long*)label_v,
-                                                (unsigned long long)old,
-                                                (unsigned long long)(key | kQueuedBit));
-    if (prev == old) return (old & kQueuedBit) ? 1 : 2;
-    old = prev;
-  }
-  return 0;
 }
 
 // Relax the merged edge lists of the items held by lanes [0, n): lane j owns
@@ -305,11 +123,6 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
   return true;
 }
 
-#ifndef BFQ_EDGE_GROUPS
-#define BFQ_EDGE_GROUPS 4
-#endif
-constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per warp step
-
 // Publish the hub chunks [c0_j, c0_j + nch_j) of the lanes with nch > 0 to
 // the chunk sub-queues.  Chunks that find no room are relaxed right here.
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
@@ -354,13 +167,6 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
   return true;
 }
 
-__device__ __forceinline__ int share_of(int cnt, int max_items, int share) {
-  return min(max_items, max(1, (cnt + share - 1) / share));
-}
-
-#ifndef BFQ_MIN_CTAS_PER_SM
-#define BFQ_MIN_CTAS_PER_SM 4
-#endif
 __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_kernel(SsspArgs a) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
