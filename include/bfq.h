@@ -226,6 +226,37 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
                        const int32_t* src, int32_t* const* dist,
                        int32_t* const* hops, bfq_tune* out, void* stream);
 
+/* ---- serving: continuous batching on a resident kernel ------------------- */
+/* A server keeps the graphs (host array of handles that must outlive it)
+ * resident and runs requests on one resident persistent kernel.  Requests
+ * are admitted in arrival order when one of max_slots (<= 2048) query slots
+ * is free and the label pool -- hbm_budget_bytes / 24 labels, each label
+ * taking 8 B plus 16 B of sub-queue capacity -- has a contiguous run for the
+ * graph's V labels; admitted requests join the queries already running on the
+ * device.  A host thread drives admission and completion.  tune may be NULL. */
+int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
+                      int64_t hbm_budget_bytes, int32_t max_slots, const bfq_tune* tune);
+/* Queue a request (thread-safe).  dist / hops: caller-owned device arrays of
+ * the graph's V int32 (either may be NULL).  The server writes them from its
+ * own stream, unordered with the caller's streams: they must hold no pending
+ * work of the caller at submission and stay valid until the request
+ * completes.  *req_id receives the request's id.  BFQ_ERR_BUDGET if the
+ * graph can never fit the budget. */
+int bfq_server_submit(bfq_server_t sv, int32_t graph_id, int32_t src, int32_t* dist,
+                      int32_t* hops, int64_t* req_id);
+/* BFQ_PENDING while the request runs or waits, else BFQ_OK with *status the
+ * request's status and the host steady-clock times (ns) of submission and of
+ * completion as seen by the server thread. */
+int bfq_server_poll(bfq_server_t sv, int64_t req_id, int32_t* status,
+                    int64_t* t_submit_ns, int64_t* t_done_ns);
+/* Wait up to timeout_ms for a request; BFQ_PENDING if it is still running. */
+int bfq_server_wait(bfq_server_t sv, int64_t req_id, int64_t timeout_ms, int32_t* status);
+/* Requests completed, kernel launches so far, most requests admitted at once. */
+int bfq_server_stats(bfq_server_t sv, int64_t* completed, int64_t* launches,
+                     int64_t* peak_active);
+/* Finish admitted requests, stop the kernel and free everything. */
+int bfq_server_destroy(bfq_server_t sv);
+
 /* ---- standalone Broker Queue (Sec. III-A, Algorithm 1; Sec. IV workloads) */
 /* A ring of `capacity` int32 items (rounded up to a power of two for the
  * warp variant), variant = BFQ_QUEUE_*. */

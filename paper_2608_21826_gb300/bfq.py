@@ -75,6 +75,15 @@ _SIGNATURES = {
     "bfq_batch_set_tune": ([_VP, ctypes.POINTER(Tune)], ctypes.c_int),
     "bfq_batch_autotune": ([_VP, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(Tune), _VP],
                            ctypes.c_int),
+    "bfq_server_create": ([ctypes.POINTER(_VP), _VP, _I32, _I64, _I32, ctypes.POINTER(Tune)],
+                          ctypes.c_int),
+    "bfq_server_submit": ([_VP, _I32, _I32, _VP, _VP, ctypes.POINTER(_I64)], ctypes.c_int),
+    "bfq_server_poll": ([_VP, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                         ctypes.POINTER(_I64)], ctypes.c_int),
+    "bfq_server_wait": ([_VP, _I64, _I64, ctypes.POINTER(_I32)], ctypes.c_int),
+    "bfq_server_stats": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                          ctypes.POINTER(_I64)], ctypes.c_int),
+    "bfq_server_destroy": ([_VP], ctypes.c_int),
     "bfq_queue_create": ([ctypes.POINTER(_VP), _I64, _I32], ctypes.c_int),
     "bfq_queue_destroy": ([_VP], ctypes.c_int),
     "bfq_queue_reset": ([_VP, _VP], ctypes.c_int),
@@ -285,6 +294,49 @@ def bfq_batch_autotune(b, graph_id, src, dist, hops=None, stream=None) -> Tune:
                                     _ptr_array(hops, n) if hops is not None else None,
                                     ctypes.byref(t), _stream(stream)))
     return t
+
+
+# ---- serving -----------------------------------------------------------------------
+
+def bfq_server_create(graphs, hbm_budget_bytes: int, max_slots: int, tune: Tune | None = None):
+    hs = (_VP * len(graphs))(*[g.value if isinstance(g, _VP) else g for g in graphs])
+    h = _VP()
+    _check(lib().bfq_server_create(ctypes.byref(h), hs, len(graphs), int(hbm_budget_bytes),
+                                   int(max_slots), ctypes.byref(tune) if tune else None))
+    return h
+
+
+def bfq_server_submit(sv, graph_id: int, src: int, dist=None, hops=None) -> int:
+    rid = _I64()
+    _check(lib().bfq_server_submit(sv, int(graph_id), int(src), _ptr(dist), _ptr(hops),
+                                   ctypes.byref(rid)))
+    return rid.value
+
+
+def bfq_server_poll(sv, req_id: int):
+    """(rc, status, t_submit_ns, t_done_ns); rc is PENDING while not done."""
+    st, t0, t1 = _I32(), _I64(), _I64()
+    rc = _check(lib().bfq_server_poll(sv, int(req_id), ctypes.byref(st), ctypes.byref(t0),
+                                      ctypes.byref(t1)))
+    return rc, st.value, t0.value, t1.value
+
+
+def bfq_server_wait(sv, req_id: int, timeout_ms: int = 60000) -> int:
+    st = _I32()
+    rc = _check(lib().bfq_server_wait(sv, int(req_id), int(timeout_ms), ctypes.byref(st)))
+    if rc == PENDING:
+        raise BfqError(ERR_TIMEOUT, f"request {req_id} still pending after {timeout_ms} ms")
+    return st.value
+
+
+def bfq_server_stats(sv):
+    a, b, c = _I64(), _I64(), _I64()
+    _check(lib().bfq_server_stats(sv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"completed": a.value, "launches": b.value, "peak_active": c.value}
+
+
+def bfq_server_destroy(sv) -> None:
+    _check(lib().bfq_server_destroy(sv))
 
 
 # ---- standalone queue ----------------------------------------------------------

@@ -19,7 +19,7 @@
 #include <new>
 #include <vector>
 
-#include "sssp_common.cuh"
+#include "sssp_multi.cuh"
 
 namespace bfq {
 
@@ -72,8 +72,6 @@ struct BatchArgs {
 
 namespace {
 
-constexpr int kCounterStride = 8;   // one 32-byte sector per query counter
-
 __device__ __forceinline__ int find_query(const int* off, int nq, int x) {
   int lo = 0, hi = nq - 1;                  // largest q with off[q] <= x
   while (lo < hi) {
@@ -83,139 +81,9 @@ __device__ __forceinline__ int find_query(const int* off, int nq, int x) {
   return lo;
 }
 
-__device__ __forceinline__ void drop_query(const BatchArgs& a, int q, int bits) {
-  atomicOr(&a.qstatus[q], bits);
-}
-
 __device__ __forceinline__ void batch_timeout(const BatchArgs& a) {
   atomicOr(&a.ctl->status, kStTimeout);
   st_relaxed_s32(&a.ctl->stop, 1);
-}
-
-// Count the buffered children (items + their queries) in their queries'
-// in-flight counters, then publish the items.
-__device__ __forceinline__ bool flush_multi(const BatchArgs& a, int home, unsigned* buf,
-                                            unsigned short* bufq, int& nbuf, int lane,
-                                            long long spin_limit, WarpCounters& wc) {
-  if (nbuf == 0) return true;
-  __syncwarp();
-  for (int i = 0; i < nbuf; i += 32) {
-    const int idx = i + lane;
-    const int q = idx < nbuf ? (int)bufq[idx] : -1;
-    const unsigned m = __match_any_sync(kFullMask, q);
-    if (q >= 0 && lane == __ffs(m) - 1) red_add_relaxed_s32(&a.inflight[q * kCounterStride], __popc(m));
-  }
-  if (lane == 0) wc.enq += nbuf;
-  __syncwarp();
-  const bool ok = enqueue_buffer(a.qs, home, buf, nbuf, lane, spin_limit, 4LL * a.qs.Q + 64);
-  __syncwarp();
-  if (!ok && lane == 0) {
-    atomicOr(&a.ctl->status, kStQueue);
-    st_relaxed_s32(&a.ctl->stop, 1);
-  }
-  nbuf = 0;
-  return ok;
-}
-
-// Merged relaxation of a mixed batch: lane j owns edges [0, deg_j) at
-// eptr_j of a tail with label lab_j in query q_j (label slice lbase_j).
-template <int U>
-__device__ __forceinline__ bool relax_multi(const BatchArgs& a, const int* s_loff, int n,
-                                            const int2* eptr, int deg, long long lab,
-                                            long long* lbase, int Vq, int q, int lane, int home,
-                                            long long spin_limit, WarpCounters& wc, unsigned* buf,
-                                            unsigned short* bufq, int& nbuf) {
-  int total = 0;
-  const int excl = warp_excl_scan(deg, lane, &total);
-  wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
-  for (int base = 0; base < total; base += 32 * U) {
-    int2 cw[U];
-    long long lab_t[U];
-    long long* lb[U];
-    int qq[U], vv[U];
-    bool act[U];
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      act[g] = false;
-      cw[g] = make_int2(0, 0);
-      lab_t[g] = 0;
-      lb[g] = nullptr;
-      qq[g] = 0;
-      vv[g] = 0;
-      if (base + 32 * g < total) {
-        const int t = base + 32 * g + lane;
-        const int j = owner_lane(excl, t, n);
-        const int ex_j = __shfl_sync(kFullMask, excl, j);
-        const int2* ep = (const int2*)__shfl_sync(kFullMask, (unsigned long long)eptr, j);
-        lb[g] = (long long*)__shfl_sync(kFullMask, (unsigned long long)lbase, j);
-        lab_t[g] = __shfl_sync(kFullMask, lab, j);
-        qq[g] = __shfl_sync(kFullMask, q, j);
-        vv[g] = __shfl_sync(kFullMask, Vq, j);
-        if (t < total) {
-          act[g] = true;
-          cw[g] = __ldg(ep + (t - ex_j));
-        }
-      }
-    }
-    long long key[U], cur[U];
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      key[g] = 0;
-      cur[g] = 0;
-      if (act[g]) {
-        const long long nd = (long long)label_dist(lab_t[g]) + (long long)cw[g].y;
-        if (nd >= (long long)kInf32) {
-          act[g] = false;
-        } else if (nd <= -2147483648LL) {
-          drop_query(a, qq[g], kStRange);
-          act[g] = false;
-        } else {
-          key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
-          cur[g] = ld_relaxed_s64(lb[g] + cw[g].x);
-        }
-      }
-    }
-    bool enq[U];
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      enq[g] = false;
-      if (act[g]) {
-        const int r = lower_label(lb[g] + cw[g].x, key[g], cur[g]);
-        if (r) {
-          ++wc.upd;
-          if (label_hops(key[g]) >= (unsigned)vv[g]) drop_query(a, qq[g], kStNegCycle);
-          else enq[g] = (r == 2);
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < U; ++g) {
-      const unsigned m = __ballot_sync(kFullMask, enq[g]);
-      if (m) {
-        if (nbuf + __popc(m) > kChildBuf) {
-          if (!flush_multi(a, home, buf, bufq, nbuf, lane, spin_limit, wc)) return false;
-        }
-        if (enq[g]) {
-          const int slot = nbuf + __popc(m & ((1u << lane) - 1u));
-          buf[slot] = (unsigned)(s_loff[qq[g]] + cw[g].x);
-          bufq[slot] = (unsigned short)qq[g];
-        }
-        nbuf += __popc(m);
-      }
-    }
-  }
-  return true;
-}
-
-// Retire the lanes' items: per query, subtract its count; the warp whose
-// subtraction empties a query also retires the query.
-__device__ __forceinline__ void retire_multi(const BatchArgs& a, int q, int lane) {
-  const unsigned m = __match_any_sync(kFullMask, q);
-  if (q >= 0 && lane == __ffs(m) - 1) {
-    const int cnt = __popc(m);
-    const int old = atomicAdd(&a.inflight[q * kCounterStride], -cnt);
-    if (old == cnt) atomicAdd(&a.ctl->remaining, -1);
-  }
 }
 
 __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_kernel(BatchArgs a) {
@@ -243,6 +111,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
   unsigned short* bufq = s_childq[wid];
   int nbuf = 0;
   WarpCounters wc;
+  const MultiEnv env{a.label, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop, a.qs,
+                     hdr.spin_limit};
   const unsigned long long t_start = globaltimer_ns();
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
@@ -381,9 +251,9 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
             cdeg = ct.z - ct.y;
             cV = d.V;
           }
-          if (!relax_multi<kGroups>(a, s_loff, 1, cep, cdeg, clab, clb, cV, cq_q, lane, home,
-                                    hdr.spin_limit, wc, buf, bufq, nbuf) ||
-              !flush_multi(a, home, buf, bufq, nbuf, lane, hdr.spin_limit, wc)) {
+          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cq_q, lane, home, wc, buf,
+                                    bufq, nbuf) ||
+              !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             timed_out = true;
             break;
           }
@@ -393,14 +263,14 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       }
       if (timed_out) break;
     }
-    if (!relax_multi<kGroups>(a, s_loff, got, eptr, deg, lab, lbase, Vq, q, lane, home,
-                              hdr.spin_limit, wc, buf, bufq, nbuf) ||
-        !flush_multi(a, home, buf, bufq, nbuf, lane, hdr.spin_limit, wc)) {
+    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, lane, home, wc, buf,
+                              bufq, nbuf) ||
+        !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       timed_out = true;
       break;
     }
     __syncwarp();
-    retire_multi(a, lane < got ? q : -1, lane);
+    if (retire_multi(env, lane < got ? q : -1, lane) >= 0) atomicAdd(&a.ctl->remaining, -1);
     int stop = 0;
     if (lane == 0) stop = ld_relaxed_s32(&a.ctl->stop);
     if (__shfl_sync(kFullMask, stop, 0)) break;

@@ -1,0 +1,116 @@
+"""Serving (continuous batching on a resident kernel): every request's result
+equals its solo run and the oracle, whatever else runs beside it; admission
+by memory budget; requests that arrive while others run overlap with them."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_21826_gb300 import bfq, synth
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n_graphs=8, seed=21, vmax=20000):
+    graphs, queries = synth.workload_batched(n_graphs=n_graphs, vmin=300, vmax=vmax, seed=seed)
+    handles = [gpu_util.create(g) for g in graphs]
+    return graphs, queries, handles
+
+
+def _solo(handles, graphs, gi, s):
+    return gpu_util.run(handles[gi], graphs[gi].V, int(s))
+
+
+def test_results_match_solo_and_oracle():
+    import torch
+    graphs, queries, handles = _setup()
+    sv = bfq.bfq_server_create(handles, 1 << 30, 64)
+    try:
+        bufs = []
+        for gi, s in queries:
+            d = torch.full((graphs[gi].V,), -3, dtype=torch.int32, device="cuda")
+            bufs.append((gi, s, d, torch.full_like(d, -3)))
+        torch.cuda.synchronize()        # buffers ready before the server writes them
+        outs = [(bfq.bfq_server_submit(sv, int(gi), int(s), d, h), gi, s, d, h)
+                for gi, s, d, h in bufs]
+        for rid, gi, s, d, h in outs:
+            st = bfq.bfq_server_wait(sv, rid, 60000)
+            sst, sd, sh, _ = _solo(handles, graphs, gi, s)
+            assert st == sst
+            g = graphs[gi]
+            ost, od, oh, _ = oracle.spfa(g.row_ptr, g.col, g.w, int(s))
+            assert st == ost
+            if st == bfq.OK:
+                assert np.array_equal(d.cpu().numpy(), sd) and np.array_equal(d.cpu().numpy(), od)
+                assert np.array_equal(h.cpu().numpy(), sh) and np.array_equal(h.cpu().numpy(), oh)
+        stats = bfq.bfq_server_stats(sv)
+        assert stats["completed"] == len(queries)
+        assert stats["peak_active"] > 1
+    finally:
+        bfq.bfq_server_destroy(sv)
+        for h in handles:
+            bfq.bfq_graph_destroy(h)
+
+
+def test_budget_admission_and_rejection():
+    import torch
+    g_small = synth.grid_graph(40, 40, seed=3)
+    g_big = synth.workload_rmat(16)
+    handles = [gpu_util.create(g_small), gpu_util.create(g_big)]
+    # room for the big graph's labels once (plus page rounding), not twice
+    budget = 24 * (((g_big.V + 4095) // 4096) * 4096 + 4096)
+    sv = bfq.bfq_server_create(handles, budget, 8)
+    try:
+        outs = []
+        for k in range(6):
+            gi = k % 2
+            g = [g_small, g_big][gi]
+            s = int(g.sources[k % len(g.sources)])
+            d = torch.empty(g.V, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            outs.append((bfq.bfq_server_submit(sv, gi, s, d), gi, s, d))
+        for rid, gi, s, d in outs:
+            assert bfq.bfq_server_wait(sv, rid, 60000) == bfq.OK
+            sst, sd, _, _ = gpu_util.run(handles[gi], [g_small, g_big][gi].V, s)
+            assert np.array_equal(d.cpu().numpy(), sd)
+        g_huge = synth.workload_rmat(17)
+        h3 = gpu_util.create(g_huge)
+        sv2 = bfq.bfq_server_create([h3], budget, 4)
+        with pytest.raises(bfq.BfqError) as e:
+            bfq.bfq_server_submit(sv2, 0, int(g_huge.sources[0]))
+        assert e.value.code == bfq.ERR_BUDGET
+        bfq.bfq_server_destroy(sv2)
+        bfq.bfq_graph_destroy(h3)
+    finally:
+        bfq.bfq_server_destroy(sv)
+        for h in handles:
+            bfq.bfq_graph_destroy(h)
+
+
+def test_arrivals_during_running_queries_and_idle_gaps():
+    """Requests trickle in (some while others run, some after the kernel went
+    idle and left); all finish with exact results."""
+    import torch
+    graphs, queries, handles = _setup(n_graphs=6, seed=31, vmax=60000)
+    sv = bfq.bfq_server_create(handles, 1 << 30, 16)
+    try:
+        outs = []
+        rng = np.random.default_rng(0)
+        for k, (gi, s) in enumerate(queries[:40]):
+            d = torch.empty(graphs[gi].V, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            outs.append((bfq.bfq_server_submit(sv, int(gi), int(s), d), gi, s, d))
+            time.sleep(float(rng.exponential(0.0005)) if k != 20 else 0.05)
+        for rid, gi, s, d in outs:
+            st = bfq.bfq_server_wait(sv, rid, 60000)
+            sst, sd, _, _ = _solo(handles, graphs, gi, s)
+            assert st == sst
+            if st == bfq.OK:
+                assert np.array_equal(d.cpu().numpy(), sd)
+        assert bfq.bfq_server_stats(sv)["launches"] >= 1
+    finally:
+        bfq.bfq_server_destroy(sv)
+        for h in handles:
+            bfq.bfq_graph_destroy(h)
