@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -43,6 +45,10 @@ def parse():
                    help="scale of the rmat22 workload (smaller only for profiling captures)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=2000,
+                   help="requests per arrival rate in the serving leg")
     return p.parse_args()
 
 
@@ -178,6 +184,170 @@ def cpu_baseline(g, n_sources=1):
                       f"{t_total:.1f} s on 1 core of {os.cpu_count()}"}
 
 
+def batched_leg(dev, reps=5):
+    """The batched mix: 64 graphs (V log-uniform in [1e3,1e6], degree U[4,16],
+    grid / R-MAT alternating, 6 with a planted negative cycle), 8 sources each
+    = 512 queries in one launch (captured CUDA graph, autotuned), against the
+    same 512 queries launched back to back on one stream."""
+    import torch
+    from paper_2608_21826_gb300 import bfq, synth
+    graphs, queries = synth.workload_batched()
+    handles = [bfq.bfq_graph_create(g.row_ptr, g.col, g.w) for g in graphs]
+    nq = len(queries)
+    total = int(sum(graphs[g].V for g, _ in queries))
+    b = bfq.bfq_batch_create(handles, nq, total)
+    dist = [torch.empty(graphs[g].V, dtype=torch.int32, device=dev) for g, _ in queries]
+    tune = bfq.bfq_batch_autotune(b, queries[:, 0], queries[:, 1], dist)
+    for _ in range(2):
+        bfq.bfq_sssp_batch(b, queries[:, 0], queries[:, 1], dist)
+    ms = []
+    for _ in range(reps):
+        rc, st = bfq.bfq_sssp_batch(b, queries[:, 0], queries[:, 1], dist)
+        ms.append(bfq.bfq_batch_get_stats(b)["kernel_ms"])
+    n_cyc = int(np.sum(st == bfq.NEG_CYCLE))
+    n_ok = int(np.sum(st == bfq.OK))
+    # m_reached per query (untimed solo pass with stats), then plain timing
+    m_reached = 0
+    for i, (gi, s) in enumerate(queries):
+        if st[i] == bfq.OK:
+            bfq.bfq_sssp(handles[gi], int(s), dist[i])
+            m_reached += bfq.bfq_get_stats(handles[gi])["m_reached"]
+    stream = torch.cuda.current_stream(dev)
+    status = torch.zeros(nq, dtype=torch.int32, device=dev)
+    plain_ms = []
+    for rep in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, (gi, s) in enumerate(queries):
+            bfq.bfq_sssp_async(handles[gi], int(s), dist[i], None, None, status[i:i + 1], stream)
+        e1.record(stream)
+        e1.synchronize()
+        if rep:
+            plain_ms.append(e0.elapsed_time(e1))
+    t_b = float(np.median(ms))
+    t_p = float(np.median(plain_ms))
+    out = {"workload": "batched64: 64 graphs, 512 queries (6 graphs with planted cycles)",
+           "queries": nq, "graphs": len(graphs), "total_vertices": total,
+           "total_edges": int(sum(g.E for g in graphs)),
+           "ms_per_batch": t_b, "qps": nq / (t_b / 1e3),
+           "plain_ms": t_p, "plain_qps": nq / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
+           "gteps": m_reached / (t_b / 1e3) / 1e9, "neg_cycle_queries": n_cyc, "ok_queries": n_ok,
+           "tune": {"share_div": tune.share_div, "chunk_batch": tune.chunk_batch,
+                    "batch_items": tune.batch_items},
+           "timing": "CUDA events around the captured graph launch (batch) and around the "
+                     "512 back-to-back bfq_sssp_async calls (plain)"}
+    bfq.bfq_batch_destroy(b)
+    return out, graphs, handles, queries
+
+
+def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7):
+    """Poisson arrivals of requests over the batched mix plus an R-MAT scale-23
+    graph, at {0.25, 0.5, 0.75, 0.9, 1.1} x the batched saturation q/s;
+    latency = submission to completion seen by the server thread.  Baseline:
+    the same arrival schedule served one request at a time with plain
+    launches (bfq_sssp) in arrival order."""
+    import torch
+    from paper_2608_21826_gb300 import bfq, synth
+    g23 = synth.workload_rmat(23)
+    h23 = bfq.bfq_graph_create(g23.row_ptr, g23.col, g23.w)
+    all_g = list(graphs) + [g23]
+    all_h = list(handles) + [h23]
+    rng = np.random.default_rng(seed)
+    # output buffers: a small ring per graph, reused once its request is done
+    ring = 6
+    bufs = [[torch.empty(g.V, dtype=torch.int32, device=dev) for _ in range(ring)] for g in all_g]
+    torch.cuda.synchronize()
+    budget = 32 * 700_000_000              # label pool of 700M labels (22.4 GB)
+    sv = bfq.bfq_server_create(all_h, budget, 512)
+    try:
+        return _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_qps,
+                           n_req)
+    finally:
+        bfq.bfq_server_destroy(sv)
+        bfq.bfq_graph_destroy(h23)
+
+
+def _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_qps, n_req):
+    srcs = [np.asarray(g.sources) for g in all_g]
+
+    def wait(rid):
+        try:
+            return bfq.bfq_server_wait(sv, rid, 60000)
+        except bfq.BfqError as e:
+            raise RuntimeError(f"serve: request {rid} stuck; server state "
+                               f"{bfq.bfq_server_state(sv)}") from e
+
+    def schedule(rate):
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        gi = rng.integers(0, len(all_g), size=n_req)
+        si = [int(srcs[g][rng.integers(0, len(srcs[g]))]) for g in gi]
+        return np.cumsum(gaps), gi, si
+
+    def run_server(times, gi, si):
+        owner = [[None] * ring for _ in all_g]
+        nxt = [0] * len(all_g)
+        ids = []
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            while time.perf_counter() - t0 < times[k]:
+                pass
+            g = int(gi[k])
+            j = nxt[g]
+            nxt[g] = (j + 1) % ring
+            if owner[g][j] is not None:
+                wait(owner[g][j])
+            rid = bfq.bfq_server_submit(sv, g, si[k], bufs[g][j])
+            owner[g][j] = rid
+            ids.append(rid)
+        lat, t_first, t_last = [], None, None
+        for rid in ids:
+            wait(rid)
+            rc, st, ts, td = bfq.bfq_server_poll(sv, rid)
+            lat.append((td - ts) / 1e6)
+            t_first = ts if t_first is None else min(t_first, ts)
+            t_last = td if t_last is None else max(t_last, td)
+        return lat, n_req / ((t_last - t_first) / 1e9)
+
+    def run_plain(times, gi, si):
+        stream = torch.cuda.current_stream(dev)
+        lat = []
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            while time.perf_counter() - t0 < times[k]:
+                pass
+            g = int(gi[k])
+            bfq.bfq_sssp(all_h[g], si[k], bufs[g][0], None, None, stream)
+            lat.append((time.perf_counter() - t0 - times[k]) * 1e3)
+        return lat, n_req / (time.perf_counter() - t0)
+
+    # saturation of the server: a burst of requests
+    times = np.zeros(min(n_req, 1024))
+    gi = rng.integers(0, len(all_g), size=len(times))
+    si = [int(srcs[g][rng.integers(0, len(srcs[g]))]) for g in gi]
+    n_keep = n_req
+    n_req = len(times)
+    _, burst_qps = run_server(times, gi, si)
+    n_req = n_keep
+    rates = []
+    for f in (0.25, 0.5, 0.75, 0.9, 1.1):
+        rate = f * sat_qps
+        times, gi, si = schedule(rate)
+        lat, qps = run_server(times, gi, si)
+        plat, pqps = run_plain(times, gi, si)
+        rates.append({"offered_qps": rate, "fraction_of_batched_saturation": f,
+                      "served_qps": qps, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)),
+                      "plain_qps": pqps, "plain_p50_ms": float(np.percentile(plat, 50)),
+                      "plain_p99_ms": float(np.percentile(plat, 99))})
+    stats = bfq.bfq_server_stats(sv)
+    return {"workload": "serve: batched mix + R-MAT 23 (V=8,388,608), Poisson arrivals",
+            "requests_per_rate": n_req, "batched_saturation_qps": sat_qps,
+            "burst_qps": burst_qps, "rates": rates, "server": stats,
+            "budget_bytes": budget, "slots": 512,
+            "latency": "host steady clock, submission to completion observed by the server"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -307,9 +477,24 @@ def run_ours(args):
                "note": "bfq_sssp (host-synchronous) per source + copy of dist to pinned host; "
                        "sources pass by value, the graph is resident"}
 
+    bfq.bfq_graph_destroy(h)
     if rank != 0:
-        bfq.bfq_graph_destroy(h)
         return
+    batched = serve = None
+    if not args.no_batched:
+        bhandles = []
+        try:
+            batched, bgraphs, bhandles, _ = batched_leg(dev)
+            if not args.no_serve:
+                try:
+                    serve = serve_leg(dev, bgraphs, bhandles, batched["qps"],
+                                      args.serve_requests)
+                except Exception as e:                       # reported, not fatal
+                    serve = {"error": repr(e)}
+        except Exception as e:
+            batched = {"error": repr(e)}
+        for hh in bhandles:
+            bfq.bfq_graph_destroy(hh)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(g, 1)
@@ -335,9 +520,10 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": 3 * n_q,
         "clocks": clk,
+        "batched": batched,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
-    bfq.bfq_graph_destroy(h)
 
 
 def main():

@@ -230,8 +230,9 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
 /* A server keeps the graphs (host array of handles that must outlive it)
  * resident and runs requests on one resident persistent kernel.  Requests
  * are admitted in arrival order when one of max_slots (<= 2048) query slots
- * is free and the label pool -- hbm_budget_bytes / 24 labels, each label
- * taking 8 B plus 16 B of sub-queue capacity -- has a contiguous run for the
+ * is free and the label pool -- hbm_budget_bytes / 32 labels, each label
+ * taking 8 B, 8 B of recorded relaxation edge and 16 B of sub-queue
+ * capacity -- has a contiguous run for the
  * graph's V labels; admitted requests join the queries already running on the
  * device.  A host thread drives admission and completion.  tune may be NULL. */
 int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
@@ -254,6 +255,11 @@ int bfq_server_wait(bfq_server_t sv, int64_t req_id, int64_t timeout_ms, int32_t
 /* Requests completed, kernel launches so far, most requests admitted at once. */
 int bfq_server_stats(bfq_server_t sv, int64_t* completed, int64_t* launches,
                      int64_t* peak_active);
+/* Monitoring snapshot, out[0..min(n,10)): requests waiting, requests
+ * admitted, free slots, largest free label run, kernel launches, requests
+ * completed, kernel running (0/1), CUDA error that stopped the server (0 =
+ * none), first failed device range check (0 = none) and its value. */
+int bfq_server_state(bfq_server_t sv, int64_t* out, int32_t n);
 /* Finish admitted requests, stop the kernel and free everything. */
 int bfq_server_destroy(bfq_server_t sv);
 

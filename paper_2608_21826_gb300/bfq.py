@@ -83,6 +83,7 @@ _SIGNATURES = {
     "bfq_server_wait": ([_VP, _I64, _I64, ctypes.POINTER(_I32)], ctypes.c_int),
     "bfq_server_stats": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                           ctypes.POINTER(_I64)], ctypes.c_int),
+    "bfq_server_state": ([_VP, _VP, _I32], ctypes.c_int),
     "bfq_server_destroy": ([_VP], ctypes.c_int),
     "bfq_queue_create": ([ctypes.POINTER(_VP), _I64, _I32], ctypes.c_int),
     "bfq_queue_destroy": ([_VP], ctypes.c_int),
@@ -333,6 +334,16 @@ def bfq_server_stats(sv):
     a, b, c = _I64(), _I64(), _I64()
     _check(lib().bfq_server_stats(sv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"completed": a.value, "launches": b.value, "peak_active": c.value}
+
+
+_STATE_KEYS = ("waiting", "admitted", "free_slots", "largest_free_labels", "launches",
+               "completed", "kernel_running", "cuda_error", "bad_check", "bad_value")
+
+
+def bfq_server_state(sv) -> dict:
+    out = np.zeros(len(_STATE_KEYS), dtype=np.int64)
+    _check(lib().bfq_server_state(sv, _ptr(out), len(out)))
+    return dict(zip(_STATE_KEYS, (int(x) for x in out)))
 
 
 def bfq_server_destroy(sv) -> None:

@@ -61,6 +61,7 @@ struct BatchArgs {
   const int* coff;              // [nq + 1] chunk-item offsets
   const QueryDesc* desc;        // [nq]
   long long* label;             // pool
+  long long* cyc;               // recorded relaxation edges, like the pool
   QueueSet qs, cq;
   int* inflight;                // [maxq * kCounterStride]
   int* qstatus;                 // [maxq]
@@ -111,8 +112,9 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
   unsigned short* bufq = s_childq[wid];
   int nbuf = 0;
   WarpCounters wc;
-  const MultiEnv env{a.label, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop, a.qs,
-                     hdr.spin_limit};
+  const MultiEnv env{a.label, a.cyc, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop,
+                     a.qs, hdr.spin_limit};
+  unsigned walk_at = kCycWalkAt;
   const unsigned long long t_start = globaltimer_ns();
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
     if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
 
     // decode the lanes' items
-    int q = -1, deg = 0, nch = 0, c0 = 0, Vq = 0;
+    int q = -1, deg = 0, nch = 0, c0 = 0, Vq = 0, tail = 0;
     long long lab = 0;
     long long* lbase = nullptr;
     const int2* eptr = nullptr;
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
         q = find_query(s_coff, nq, (int)item);
         const QueryDesc& d = a.desc[q];
         const int4 ct = d.chunk_tab[(int)item - s_coff[q]];
+        tail = ct.x;
         lbase = a.label + s_loff[q];
         lab = label_key(ld_relaxed_s64(lbase + ct.x));
         eptr = d.adj + ct.y;
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       } else {
         q = find_query(s_loff, nq, (int)item);
         const int u = (int)item - s_loff[q];
+        tail = u;
         const QueryDesc& d = a.desc[q];
         lbase = a.label + s_loff[q];
         lab = label_key((long long)atomicAnd((unsigned long long*)(lbase + u),
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
         while (left) {
           const unsigned cid = __shfl_sync(kFullMask, id, __ffs(left) - 1);
           left &= left - 1;
-          int cq_q = -1, cdeg = 0, cV = 0;
+          int cq_q = -1, cdeg = 0, cV = 0, ctail = 0;
           long long clab = 0;
           long long* clb = nullptr;
           const int2* cep = nullptr;
@@ -250,9 +254,10 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
             cep = d.adj + ct.y;
             cdeg = ct.z - ct.y;
             cV = d.V;
+            ctail = ct.x;
           }
-          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cq_q, lane, home, wc, buf,
-                                    bufq, nbuf) ||
+          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cq_q, ctail, lane, home,
+                                    wc, buf, bufq, nbuf, walk_at) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             timed_out = true;
             break;
@@ -263,8 +268,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       }
       if (timed_out) break;
     }
-    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, lane, home, wc, buf,
-                              bufq, nbuf) ||
+    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+                              buf, bufq, nbuf, walk_at) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       timed_out = true;
       break;
@@ -541,6 +546,7 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
 #define B_TRY(x) do { rc = (x); if (rc != BFQ_OK) { delete b; return rc; } } while (0)
   B_TRY(b->alloc((void**)&b->stage_dev, b->stage_bytes));
   B_TRY(b->alloc((void**)&a.label, sizeof(long long) * (size_t)max_total_vertices));
+  B_TRY(b->alloc((void**)&a.cyc, sizeof(long long) * (size_t)max_total_vertices));
   B_TRY(b->alloc((void**)&a.qs.meta, sizeof(QueueMeta) * Q));
   B_TRY(b->alloc((void**)&a.qs.slots, sizeof(unsigned long long) * ((size_t)Q << a.qs.cap_log2)));
   B_TRY(b->alloc((void**)&a.cq.meta, sizeof(QueueMeta) * a.cq.Q));
@@ -555,6 +561,7 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
   a.coff = (const int*)(b->stage_dev + o_coff);
   a.desc = (const QueryDesc*)(b->stage_dev + o_desc);
 #define B_CUDA(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) { int r__ = cuda_fail(e__, #x, __FILE__, __LINE__); delete b; return r__; } } while (0)
+  B_CUDA(cudaMemset(a.cyc, 0xff, sizeof(long long) * (size_t)max_total_vertices));
   B_CUDA(cudaMemset(a.qs.meta, 0, sizeof(QueueMeta) * Q));
   B_CUDA(cudaMemset(a.qs.slots, 0, sizeof(unsigned long long) * ((size_t)Q << a.qs.cap_log2)));
   B_CUDA(cudaMemset(a.cq.meta, 0, sizeof(QueueMeta) * a.cq.Q));

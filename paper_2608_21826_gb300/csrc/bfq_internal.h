@@ -31,6 +31,7 @@ struct SsspArgs {
   const int* row_ptr;           // [V+1]
   const int2* adj;              // [E] (col, w)
   long long* label;             // [V] packed (dist, hops, in-queue flag)
+  long long* cyc;               // [V] recorded relaxation edges (tail, w), or null
   QueueSet qs;                  // vertex sub-queues
   QueueSet cq;                  // hub edge-chunk sub-queues
   const int* hub_chunk0;        // [V] first chunk-table entry of a hub (read for hubs only)

@@ -47,6 +47,7 @@ struct bfq_graph {
   int* row_ptr = nullptr;
   int2* adj = nullptr;
   long long* label = nullptr;
+  long long* cyc = nullptr;
   QueueSet qs{};
   QueueSet cq{};
   int* hub_chunk0 = nullptr;
@@ -266,6 +267,7 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   g->cq.Q = Qc;
   g->cq.cap_log2 = std::max(8, ceil_log2(std::max(1LL, per_qc)));
   G_TRY(g->alloc((void**)&g->label, sizeof(long long) * (size_t)V));
+  G_TRY(g->alloc((void**)&g->cyc, sizeof(long long) * (size_t)V));
   G_TRY(g->alloc((void**)&g->qs.meta, sizeof(QueueMeta) * Q));
   G_TRY(g->alloc((void**)&g->qs.slots, sizeof(unsigned long long) * ((size_t)Q << cap_log2)));
   G_TRY(g->alloc((void**)&g->cq.meta, sizeof(QueueMeta) * Qc));
@@ -274,6 +276,7 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   G_TRY(g->alloc((void**)&g->ctl, sizeof(Control)));
   G_TRY(g->alloc((void**)&g->status_dev, sizeof(int32_t)));
   G_TRY(g->alloc((void**)&g->scratch, 2 * sizeof(unsigned long long)));
+  G_CUDA(cudaMemsetAsync(g->cyc, 0xff, sizeof(long long) * (size_t)V, s));   // tail -1: none
   G_CUDA(cudaMemsetAsync(g->qs.meta, 0, sizeof(QueueMeta) * Q, s));
   G_CUDA(cudaMemsetAsync(g->qs.slots, 0, sizeof(unsigned long long) * ((size_t)Q << cap_log2), s));
   G_CUDA(cudaMemsetAsync(g->cq.meta, 0, sizeof(QueueMeta) * Qc, s));
@@ -305,6 +308,7 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.row_ptr = g->row_ptr;
   a.adj = g->adj;
   a.label = g->label;
+  a.cyc = g->cyc;
   a.qs = g->qs;
   a.cq = g->cq;
   a.hub_chunk0 = g->hub_chunk0;

@@ -168,6 +168,7 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   a.row_ptr = row_ptr;
   a.adj = (const int2*)adj;
   a.label = (long long*)(base + L.label);
+  a.cyc = nullptr;                 // cycle accelerator off: hops >= V decides alone
   a.qs = QueueSet{(QueueMeta*)(base + L.qmeta), (unsigned long long*)(base + L.qslots),
                   kNoAllocQueues, L.cap_log2};
   a.cq = QueueSet{(QueueMeta*)(base + L.cmeta), (unsigned long long*)(base + L.cslots), 1, 8};

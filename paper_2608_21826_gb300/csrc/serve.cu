@@ -59,8 +59,9 @@ struct alignas(16) SlotDesc {
   int* dist;
   int* hops;
   int V, src, hub_degree, chunk_edges;
-  int label_off, n_tasks;
+  int label_off, n_tasks, n_chunks, pad0;
   long long req_id;
+  long long pad1;
 };
 
 struct alignas(16) ServeCmd {            // mapped host memory, host -> device
@@ -91,6 +92,9 @@ struct alignas(128) ServeCtl {
   int pad4[31];
   unsigned long long ctr[8];
   unsigned long long pad5[8];
+  int bad_where;                         // first failed range check (0 = none)
+  unsigned bad_value;
+  int pad6[30];
 };
 
 struct ServeArgs {
@@ -100,12 +104,15 @@ struct ServeArgs {
   int* pending;                          // [S * kCounterStride] init/unpack tasks left
   int* page_owner;                       // [pool pages]
   long long* label;                      // pool
+  long long* cyc;                        // recorded relaxation edges, like the pool
   QueueSet qs, cq, tq;                   // vertices, hub chunks, tasks
   ServeCmd* cmd;                         // mapped ring [R]
   ServeDone* done;                       // mapped ring [R]
   const int* shutdown;                   // mapped flag
   ServeCtl* ctl;
   int ring;
+  int max_slots;
+  int pool_pages;
   int queues_per_cta;
   int share_div, chunk_batch, batch_items;
   long long spin_limit, time_limit_ns, idle_exit_ns;
@@ -133,6 +140,14 @@ __device__ __forceinline__ int atom_add_acq_rel_s32(int* p, int v) {
 
 __device__ __forceinline__ void serve_fail(const ServeArgs& a) {
   atomicOr(&a.ctl->status, kStTimeout);
+  st_relaxed_s32(&a.ctl->stop, 1);
+}
+
+// A decoded item or task out of range: record the first one, stop the
+// launch, and let the caller skip the access.
+__device__ __noinline__ void serve_bad(const ServeArgs& a, int where, unsigned value) {
+  if (atomicCAS(&a.ctl->bad_where, 0, where) == 0) a.ctl->bad_value = value;
+  atomicOr(&a.ctl->status, kStQueue);
   st_relaxed_s32(&a.ctl->stop, 1);
 }
 
@@ -184,7 +199,16 @@ __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int la
   const int kind = (int)(id >> 30);
   const int slot = (int)((id >> 19) & (kMaxSlots - 1));
   const int t = (int)(id & ((1u << 19) - 1));
+  if (slot >= a.max_slots) {
+    if (lane == 0) serve_bad(a, 1, id);
+    return false;
+  }
   const SlotDesc d = a.slots[slot];
+  if (t >= d.n_tasks || d.label_off < 0 ||
+      ((long long)d.label_off + d.V) > ((long long)a.pool_pages << kPageLog2)) {
+    if (lane == 0) serve_bad(a, 2, id);
+    return false;
+  }
   const int lo = t << kTaskLog2;
   const int hi = min(d.V, lo + (1 << kTaskLog2));
   long long* lab = a.label + d.label_off;
@@ -246,8 +270,9 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
   unsigned short* bufq = s_childq[wid];
   int nbuf = 0;
   WarpCounters wc;
-  const MultiEnv env{a.label, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop, a.qs,
-                     a.spin_limit};
+  const MultiEnv env{a.label, a.cyc, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop,
+                     a.qs, a.spin_limit};
+  unsigned walk_at = kCycWalkAt;
   const unsigned long long t_start = globaltimer_ns();
   unsigned long long t_idle = t_start;
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
@@ -310,6 +335,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
     if (got == 0) {
       // 3) admission, then idle
       if (admit_one(a, lane)) { idle = 0; continue; }
+      if (idle == 0) t_idle = globaltimer_ns();
       int leave = 0;
       if (lane == 0) {
         const unsigned long long now = globaltimer_ns();
@@ -319,7 +345,6 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
                  (long long)(now - t_idle) > a.idle_exit_ns) leave = 1;
       }
       if (__shfl_sync(kFullMask, leave, 0)) break;
-      if (idle == 0) t_idle = globaltimer_ns();
       ++wc.idle;
       __nanosleep(min(32u << min(idle, 5), 1024u));
       ++idle;
@@ -329,24 +354,40 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
     wc.deq += (lane == 0) ? (unsigned long long)got : 0ull;
     if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
 
-    int q = -1, deg = 0, nch = 0, c0 = 0, Vq = 0;
+    int q = -1, deg = 0, nch = 0, c0 = 0, Vq = 0, tail = 0;
     long long lab = 0;
     long long* lbase = nullptr;
     const int2* eptr = nullptr;
+    bool bad = false;
     if (lane < got) {
       if (is_chunk) {
         q = (int)(item >> kChunkIdBits);
-        const SlotDesc& d = a.slots[q];
-        const int4 ct = d.chunk_tab[item & ((1u << kChunkIdBits) - 1)];
-        lbase = a.label + d.label_off;
-        lab = label_key(ld_relaxed_s64(lbase + ct.x));
-        eptr = d.adj + ct.y;
-        deg = ct.z - ct.y;
-        Vq = d.V;
+        const unsigned ci = item & ((1u << kChunkIdBits) - 1);
+        if (q >= a.max_slots || (int)ci >= a.slots[q].n_chunks) {
+          serve_bad(a, 3, item);
+          bad = true;
+        } else {
+          const SlotDesc& d = a.slots[q];
+          const int4 ct = d.chunk_tab[ci];
+          tail = ct.x;
+          lbase = a.label + d.label_off;
+          lab = label_key(ld_relaxed_s64(lbase + ct.x));
+          eptr = d.adj + ct.y;
+          deg = ct.z - ct.y;
+          Vq = d.V;
+        }
+      } else if ((item >> kPageLog2) >= (unsigned)a.pool_pages ||
+                 (unsigned)a.page_owner[item >> kPageLog2] >= (unsigned)a.max_slots ||
+                 (int)item - a.slots[a.page_owner[item >> kPageLog2]].label_off < 0 ||
+                 (int)item - a.slots[a.page_owner[item >> kPageLog2]].label_off >=
+                     a.slots[a.page_owner[item >> kPageLog2]].V) {
+        serve_bad(a, 4, item);
+        bad = true;
       } else {
         q = a.page_owner[item >> kPageLog2];
         const SlotDesc& d = a.slots[q];
         const int u = (int)item - d.label_off;
+        tail = u;
         lbase = a.label + d.label_off;
         lab = label_key((long long)atomicAnd((unsigned long long*)(lbase + u),
                                              ~(unsigned long long)kQueuedBit));
@@ -360,11 +401,12 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
           deg = 0;
         }
       }
-      if (ld_relaxed_s32(&a.qstatus[q]) & (kStNegCycle | kStRange)) {
+      if (!bad && (ld_relaxed_s32(&a.qstatus[q]) & (kStNegCycle | kStRange))) {
         deg = 0;
         nch = 0;
       }
     }
+    if (__any_sync(kFullMask, bad)) break;      // the launch stops; nothing was touched
     if (__any_sync(kFullMask, nch > 0)) {
       const int qn = nch > 0 ? q : -1;
       const unsigned m = __match_any_sync(kFullMask, qn);
@@ -389,7 +431,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
         while (left) {
           const unsigned cid = __shfl_sync(kFullMask, id, __ffs(left) - 1);
           left &= left - 1;
-          int cs = -1, cdeg = 0, cV = 0;
+          int cs = -1, cdeg = 0, cV = 0, ctail = 0;
           long long clab = 0;
           long long* clb = nullptr;
           const int2* cep = nullptr;
@@ -402,9 +444,10 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
             cep = d.adj + ct.y;
             cdeg = ct.z - ct.y;
             cV = d.V;
+            ctail = ct.x;
           }
-          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cs, lane, home, wc, buf,
-                                    bufq, nbuf) ||
+          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cs, ctail, lane, home, wc,
+                                    buf, bufq, nbuf, walk_at) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             failed = true;
             break;
@@ -415,8 +458,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
       }
       if (failed) break;
     }
-    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, lane, home, wc, buf,
-                              bufq, nbuf) ||
+    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+                              buf, bufq, nbuf, walk_at) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       failed = true;
       break;
@@ -533,6 +576,9 @@ struct bfq_server {
   long long relaunches = 0, completed = 0, peak_active = 0;
   long long completed_at_launch = 0;
   int stalled_launches = 0;
+  int cuda_error = 0;
+  int bad_where = 0;
+  unsigned bad_value = 0;
   std::thread th;
 
   ~bfq_server() {
@@ -564,6 +610,26 @@ struct bfq_server {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
         .count();
+  }
+
+  // Every admitted and waiting request ends with `code`.
+  void fail_all(int code) {
+    for (auto& kv : admitted) {
+      auto rec = records.find(kv.first);
+      if (rec != records.end()) {
+        rec->second.status = code;
+        rec->second.t_done = now_ns();
+      }
+    }
+    admitted.clear();
+    for (auto& rq : pending) {
+      auto rec = records.find(rq.id);
+      if (rec != records.end()) {
+        rec->second.status = code;
+        rec->second.t_done = now_ns();
+      }
+    }
+    pending.clear();
   }
 
   bool alloc_pages(long long need, long long* start) {
@@ -644,6 +710,7 @@ struct bfq_server {
         d.hub_degree = gv.hub_degree;
         d.chunk_edges = gv.chunk_edges;
         d.label_off = (int)(start << kPageLog2);
+        d.n_chunks = gv.n_chunks;
         d.req_id = rq.id;
         c->d = d;
         c->slot = slot;
@@ -655,7 +722,15 @@ struct bfq_server {
         peak_active = std::max<long long>(peak_active, (long long)admitted.size());
       }
       // the kernel runs while anything is admitted
-      if (launched && cudaEventQuery(kernel_done) == cudaSuccess) {
+      cudaError_t qe = launched ? cudaEventQuery(kernel_done) : cudaSuccess;
+      if (launched && qe != cudaSuccess && qe != cudaErrorNotReady) {
+        // the launch failed outright: nothing more can run on this context
+        cuda_error = (int)qe;
+        fail_all(BFQ_ERR_CUDA);
+        launched = false;
+        stopping = true;
+      }
+      if (launched && qe == cudaSuccess) {
         launched = false;
         ServeCtl c;
         cudaMemcpy(&c, args.ctl, sizeof(c), cudaMemcpyDeviceToHost);
@@ -663,6 +738,10 @@ struct bfq_server {
         // while requests were admitted counts as stuck
         stalled_launches = (completed == completed_at_launch && !admitted.empty())
                                ? stalled_launches + 1 : 0;
+        if (c.bad_where) {
+          bad_where = c.bad_where;
+          bad_value = c.bad_value;
+        }
         if ((c.status & (kStTimeout | kStQueue)) || stalled_launches >= 3) {
           stalled_launches = 0;
           // a bounded wait ran out, or the kernel made no progress: fail what
@@ -735,8 +814,9 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
     sv->views.push_back(gv);
     maxC = std::max<long long>(maxC, gv.n_chunks);
   }
-  // budget: 8 B of label + 16 B of sub-queue slots per pooled label
-  long long entries = hbm_budget_bytes / 24;
+  // budget: 8 B of label + 8 B of recorded edge + 16 B of sub-queue slots
+  // per pooled label
+  long long entries = hbm_budget_bytes / 32;
   entries = (entries >> kPageLog2) << kPageLog2;
   if (entries < (1 << kPageLog2) || entries >= (1LL << 31))
     { delete sv; return s_invalid("bfq_server_create: budget must cover 4096..2^31 labels"); }
@@ -768,6 +848,8 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
     max_tasks = std::max<long long>(max_tasks, (gv.V + (1LL << kTaskLog2) - 1) >> kTaskLog2);
   a.tq.cap_log2 = std::max(10, ceil_log2_s((long long)max_slots * max_tasks));
   a.ring = sv->ring;
+  a.max_slots = max_slots;
+  a.pool_pages = (int)(entries >> kPageLog2);
   a.share_div = sv->tune.share_div;
   a.chunk_batch = sv->tune.chunk_batch;
   a.batch_items = sv->tune.batch_items;
@@ -783,6 +865,7 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   S_TRY(sv->dalloc((void**)&a.pending, sizeof(int) * kCounterStride * max_slots));
   S_TRY(sv->dalloc((void**)&a.page_owner, sizeof(int) * pages));
   S_TRY(sv->dalloc((void**)&a.label, sizeof(long long) * entries));
+  S_TRY(sv->dalloc((void**)&a.cyc, sizeof(long long) * entries));
   S_TRY(sv->dalloc((void**)&a.qs.meta, sizeof(QueueMeta) * a.qs.Q));
   S_TRY(sv->dalloc((void**)&a.qs.slots, sizeof(unsigned long long) * ((size_t)a.qs.Q << a.qs.cap_log2)));
   S_TRY(sv->dalloc((void**)&a.cq.meta, sizeof(QueueMeta) * a.cq.Q));
@@ -802,6 +885,7 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   S_CUDA(cudaHostGetDevicePointer((void**)&a.done, sv->done_host, 0));
   S_CUDA(cudaHostGetDevicePointer((void**)&a.shutdown, sv->shutdown_host, 0));
   S_CUDA(cudaMemset(a.ctl, 0, sizeof(ServeCtl)));
+  S_CUDA(cudaMemset(a.cyc, 0xff, sizeof(long long) * entries));
   S_CUDA(cudaMemset(a.inflight, 0, sizeof(int) * kCounterStride * max_slots));
   S_CUDA(cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking));
   S_CUDA(cudaEventCreateWithFlags(&sv->kernel_done, cudaEventDisableTiming));
@@ -831,6 +915,10 @@ int bfq_server_submit(bfq_server_t sv, int32_t graph_id, int32_t src, int32_t* d
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stopping) return s_invalid("bfq_server_submit: server is shutting down");
+    if (sv->cuda_error) {
+      set_error("bfq_server_submit: the server stopped after a CUDA error");
+      return BFQ_ERR_CUDA;
+    }
     const int64_t id = sv->next_id++;
     const int64_t t = bfq_server::now_ns();
     sv->pending.push_back({id, graph_id, src, dist, hops, t});
@@ -878,6 +966,19 @@ int bfq_server_stats(bfq_server_t sv, int64_t* completed, int64_t* relaunches,
   if (completed) *completed = sv->completed;
   if (relaunches) *relaunches = sv->relaunches;
   if (peak_active) *peak_active = sv->peak_active;
+  return BFQ_OK;
+}
+
+int bfq_server_state(bfq_server_t sv, int64_t* out, int32_t n) {
+  if (!sv || !out || n < 1) return s_invalid("bfq_server_state: null argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  long long largest = 0;
+  for (auto& kv : sv->free_pages) largest = std::max(largest, kv.second);
+  const int64_t v[10] = {(int64_t)sv->pending.size(), (int64_t)sv->admitted.size(),
+                         (int64_t)sv->free_slots.size(), largest << kPageLog2,
+                         sv->relaunches, sv->completed, sv->launched ? 1 : 0,
+                         sv->cuda_error, sv->bad_where, (int64_t)sv->bad_value};
+  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
   return BFQ_OK;
 }
 

@@ -48,8 +48,9 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 // capacity kChildBuf) and published in bulk by flush_children.
 template <int U>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
-                                             long long lab, int lane, int home,
-                                             WarpCounters& wc, unsigned* buf, int& nbuf) {
+                                             long long lab, int tail, int lane, int home,
+                                             WarpCounters& wc, unsigned* buf, int& nbuf,
+                                             unsigned& walk_at) {
   int total = 0;
   const int excl = warp_excl_scan(deg, lane, &total);
   wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
@@ -57,18 +58,21 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
     long long lab_t[U];
+    int tl[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       act[g] = false;
       cw[g] = make_int2(0, 0);
       lab_t[g] = 0;
+      tl[g] = 0;
       if (base + 32 * g < total) {          // warp-uniform
         const int t = base + 32 * g + lane;
         const int j = owner_lane(excl, t, n);
         const int ex_j = __shfl_sync(kFullMask, excl, j);
         const int beg_j = __shfl_sync(kFullMask, beg, j);
         lab_t[g] = __shfl_sync(kFullMask, lab, j);
+        tl[g] = __shfl_sync(kFullMask, tail, j);
         if (t < total) {
           act[g] = true;
           cw[g] = __ldg(&a.adj[beg_j + (t - ex_j)]);
@@ -103,8 +107,22 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         const int r = lower_label(&a.label[cw[g].x], key[g], cur[g]);
         if (r) {
           ++wc.upd;
-          if (label_hops(key[g]) >= V) raise_status(a.ctl, kStNegCycle);
-          else enq[g] = (r == 2);
+          const unsigned nh = label_hops(key[g]);
+          if (nh >= V) {
+            raise_status(a.ctl, kStNegCycle);
+          } else {
+            enq[g] = (r == 2);
+            if (a.cyc && nh >= kCycRecord) {
+              st_relaxed_u64((unsigned long long*)(a.cyc + cw[g].x),
+                             (unsigned long long)pack_edge(tl[g], cw[g].y));
+              if (nh >= walk_at) {
+                if (prove_negative_cycle(a.cyc, a.label, cw[g].x, a.V))
+                  raise_status(a.ctl, kStNegCycle);
+                else
+                  walk_at = nh * 2;
+              }
+            }
+          }
         }
       }
     }
@@ -127,7 +145,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
 // the chunk sub-queues.  Chunks that find no room are relaxed right here.
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
                                             int home, int chome, WarpCounters& wc,
-                                            unsigned* buf, int& nbuf) {
+                                            unsigned* buf, int& nbuf, unsigned& walk_at) {
   int K = 0;
   const int excl = warp_excl_scan(nch, lane, &K);
   if (K == 0) return true;
@@ -150,15 +168,17 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
       const int src_lane = __ffs(left) - 1;
       left &= left - 1;
       const unsigned cid = __shfl_sync(kFullMask, id, src_lane);
-      int beg = 0, deg = 0;
+      int beg = 0, deg = 0, tail = 0;
       long long lab = 0;
       if (lane == 0) {
         const int4 ct = a.chunk_tab[cid];
         beg = ct.y;
         deg = ct.z - ct.y;
+        tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged<kGroups>(a, 1, beg, deg, lab, lane, home, wc, buf, nbuf) ||
+      if (!relax_merged<kGroups>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+                                 walk_at) ||
           !flush_children(a, home, buf, nbuf, lane, wc))
         return false;
       if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -1);
@@ -183,6 +203,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   unsigned* buf = s_children[wid];
   int nbuf = 0;
+  unsigned walk_at = kCycWalkAt;      // per lane: hops that trigger a cycle walk
   for (;;) {
     unsigned item = 0;
     int got = 0;
@@ -243,16 +264,18 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
     wc.deq += (lane == 0) ? (unsigned long long)got : 0ull;
     if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
 
-    int beg = 0, deg = 0, nch = 0, c0 = 0;
+    int beg = 0, deg = 0, nch = 0, c0 = 0, tail = 0;
     long long lab = 0;
     if (lane < got) {
       if (is_chunk) {
         const int4 ct = a.chunk_tab[item];
         beg = ct.y;
         deg = ct.z - ct.y;
+        tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       } else {
         const unsigned u = item;
+        tail = (int)u;
         // clear the in-queue flag and read the label in one atomic: any
         // later improvement sees the flag clear and queues u again
         lab = label_key((long long)atomicAnd((unsigned long long*)&a.label[u],
@@ -267,12 +290,13 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks(a, nch, c0, lane, home, chome, wc, buf, nbuf)) {
+      if (!push_chunks(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at)) {
         timed_out = true;
         break;
       }
     }
-    if (!relax_merged<kGroups>(a, got, beg, deg, lab, lane, home, wc, buf, nbuf) ||
+    if (!relax_merged<kGroups>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+                               walk_at) ||
         !flush_children(a, home, buf, nbuf, lane, wc)) {
       timed_out = true;
       break;

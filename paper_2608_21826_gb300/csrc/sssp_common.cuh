@@ -156,6 +156,55 @@ __device__ __forceinline__ int lower_label(long long* label_v, long long key, lo
 #endif
 constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per warp step
 
+// Negative-cycle accelerator.  A successful relaxation that gives v a label
+// of kCycRecord hops or more records its edge (tail, weight) in cyc[v], one
+// 8-byte store.  When a label reaches `walk_at` hops the relaxing lane walks
+// the recorded edges backwards from v (Brent's cycle finding, at most
+// kCycWalk steps).  If they close a cycle, the weights are re-read around it:
+// a closed walk of real edges with negative total weight, through vertices
+// that hold finite labels in this run, proves a reachable negative cycle.
+// Nothing else is concluded from the walk, so a racy or stale record can
+// only make a proof fail, never make one up; the hops >= V test remains the
+// exact fallback.
+constexpr unsigned kCycRecord = 128;
+constexpr unsigned kCycWalkAt = 256;
+constexpr int kCycWalk = 32;
+
+__device__ __forceinline__ long long pack_edge(int tail, int w) {
+  return (long long)(((unsigned long long)(unsigned)w << 32) | (unsigned)tail);
+}
+
+__device__ __noinline__ bool prove_negative_cycle(const long long* cyc,
+                                                  const long long* label, int v, int V) {
+  long long e = ld_relaxed_s64(cyc + v);
+  int hare = (int)(unsigned)e;
+  if (hare < 0 || hare >= V) return false;
+  int tort = v, power = 1, lam = 1, steps = 1;
+  while (tort != hare) {
+    if (++steps > kCycWalk) return false;
+    if (power == lam) {
+      tort = hare;
+      power <<= 1;
+      lam = 0;
+    }
+    e = ld_relaxed_s64(cyc + hare);
+    hare = (int)(unsigned)e;
+    ++lam;
+    if (hare < 0 || hare >= V) return false;
+  }
+  long long sum = 0;
+  int x = hare;
+  for (int i = 0; i < lam; ++i) {
+    if (label_dist(ld_relaxed_s64(label + x)) == kInf32) return false;
+    e = ld_relaxed_s64(cyc + x);
+    const int y = (int)(unsigned)e;
+    if (y < 0 || y >= V) return false;
+    sum += (long long)(int)(e >> 32);
+    x = y;
+  }
+  return x == hare && sum < 0;
+}
+
 __device__ __forceinline__ int share_of(int cnt, int max_items, int share) {
   return min(max_items, max(1, (cnt + share - 1) / share));
 }

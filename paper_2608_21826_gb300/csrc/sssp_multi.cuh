@@ -13,6 +13,7 @@ constexpr int kCounterStride = 8;   // one 32-byte sector per query counter
 // Where the per-query state lives.
 struct MultiEnv {
   long long* pool;              // label pool; an item is an index into it
+  long long* cyc;               // recorded relaxation edges, indexed like pool (or null)
   int* inflight;                // [query * kCounterStride]
   int* qstatus;                 // [query] kStNegCycle / kStRange
   int* gstatus;                 // launch-wide kSt* bits
@@ -53,8 +54,9 @@ __device__ __forceinline__ bool flush_multi(const MultiEnv& e, int home, unsigne
 template <int U>
 __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2* eptr, int deg,
                                             long long lab, long long* lbase, int Vq, int q,
-                                            int lane, int home, WarpCounters& wc, unsigned* buf,
-                                            unsigned short* bufq, int& nbuf) {
+                                            int tail, int lane, int home, WarpCounters& wc,
+                                            unsigned* buf, unsigned short* bufq, int& nbuf,
+                                            unsigned& walk_at) {
   int total = 0;
   const int excl = warp_excl_scan(deg, lane, &total);
   wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
@@ -62,7 +64,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
     int2 cw[U];
     long long lab_t[U];
     long long* lb[U];
-    int qq[U], vv[U];
+    int qq[U], vv[U], tl[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
@@ -72,6 +74,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
       lb[g] = nullptr;
       qq[g] = 0;
       vv[g] = 0;
+      tl[g] = 0;
       if (base + 32 * g < total) {          // warp-uniform
         const int t = base + 32 * g + lane;
         const int j = owner_lane(excl, t, n);
@@ -81,6 +84,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
         lab_t[g] = __shfl_sync(kFullMask, lab, j);
         qq[g] = __shfl_sync(kFullMask, q, j);
         vv[g] = __shfl_sync(kFullMask, Vq, j);
+        tl[g] = __shfl_sync(kFullMask, tail, j);
         if (t < total) {
           act[g] = true;
           cw[g] = __ldg(ep + (t - ex_j));
@@ -113,8 +117,23 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
         const int r = lower_label(lb[g] + cw[g].x, key[g], cur[g]);
         if (r) {
           ++wc.upd;
-          if (label_hops(key[g]) >= (unsigned)vv[g]) atomicOr(&e.qstatus[qq[g]], kStNegCycle);
-          else enq[g] = (r == 2);
+          const unsigned nh = label_hops(key[g]);
+          if (nh >= (unsigned)vv[g]) {
+            atomicOr(&e.qstatus[qq[g]], kStNegCycle);
+          } else {
+            enq[g] = (r == 2);
+            if (e.cyc && nh >= kCycRecord) {
+              long long* cb = e.cyc + (lb[g] - e.pool);
+              st_relaxed_u64((unsigned long long*)(cb + cw[g].x),
+                             (unsigned long long)pack_edge(tl[g], cw[g].y));
+              if (nh >= walk_at) {
+                if (prove_negative_cycle(cb, lb[g], cw[g].x, vv[g]))
+                  atomicOr(&e.qstatus[qq[g]], kStNegCycle);
+                else
+                  walk_at = nh * 2;
+              }
+            }
+          }
         }
       }
     }

@@ -60,7 +60,7 @@ def test_budget_admission_and_rejection():
     g_big = synth.workload_rmat(16)
     handles = [gpu_util.create(g_small), gpu_util.create(g_big)]
     # room for the big graph's labels once (plus page rounding), not twice
-    budget = 24 * (((g_big.V + 4095) // 4096) * 4096 + 4096)
+    budget = 32 * (((g_big.V + 4095) // 4096) * 4096 + 4096)
     sv = bfq.bfq_server_create(handles, budget, 8)
     try:
         outs = []

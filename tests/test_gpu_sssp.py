@@ -243,3 +243,51 @@ def test_timeout_leaves_context_usable():
     finally:
         bfq.bfq_graph_destroy(h)
     _compare(g, int(g.sources[0]), gpu_util.sssp(g, int(g.sources[0])))
+
+
+def _path_into_cycle(n_path, cyc_w, seed=0):
+    """0 -> 1 -> ... -> n_path-1 (weights U[-3,5]) then a 5-cycle on the last
+    five path vertices closed with total weight cyc_w."""
+    rng = np.random.default_rng(seed)
+    w = rng.integers(-3, 6, size=n_path - 1).astype(np.int64)
+    u = list(range(n_path - 1))
+    v = list(range(1, n_path))
+    ww = list(w)
+    c = list(range(n_path - 5, n_path))
+    # the cycle c0 -> c1 -> ... -> c4 -> c0 reuses the path edges c0..c4 and
+    # adds the closing edge c4 -> c0
+    inner = int(sum(w[n_path - 5:n_path - 1]))
+    u.append(c[4])
+    v.append(c[0])
+    ww.append(cyc_w - inner)
+    rp, col, order = synth.csr_from_edges(n_path, np.array(u), np.array(v), return_order=True)
+    return synth.Graph("pathcycle", rp, col, np.array(ww, np.int32)[order], np.array([0], np.int32))
+
+
+@pytest.mark.parametrize("cyc_w", [-1, 0, 3])
+def test_cycle_accelerator_sound_and_fast(cyc_w):
+    """A deep path feeding a 5-cycle: the hop counts pass the walk threshold,
+    so the recorded-edge walk runs; it must report only a negative cycle (the
+    zero and positive ones are not), and quickly."""
+    g = _path_into_cycle(3000, cyc_w)
+    h = gpu_util.create(g)
+    try:
+        res = gpu_util.run(h, g.V, 0)
+        ost = _compare(g, 0, res)
+        assert ost == (oracle.NEG_CYCLE if cyc_w < 0 else oracle.OK)
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+def test_planted_cycle_detected_fast_on_large_graph():
+    """A 5-edge negative cycle in a 1M-vertex grid: hops >= V alone would need
+    ~V/5 laps of the cycle; the recorded-edge walk proves it far sooner."""
+    base = synth.grid_graph(1024, 1024, seed=13)
+    g = synth.plant_negative_cycle(base, 5, seed=2)
+    h = gpu_util.create(g)
+    try:
+        st, _, _, _ = gpu_util.run(h, g.V, 0, want_hops=False)
+        assert st == bfq.NEG_CYCLE
+        assert bfq.bfq_get_stats(h)["kernel_ms"] < 200.0
+    finally:
+        bfq.bfq_graph_destroy(h)
