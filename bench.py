@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-queue", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
     return p.parse_args()
@@ -254,8 +255,8 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7):
     all_g = list(graphs) + [g23]
     all_h = list(handles) + [h23]
     rng = np.random.default_rng(seed)
-    # output buffers: a small ring per graph, reused once its request is done
-    ring = 6
+    # output buffers: a ring per graph, a buffer reused once its request is done
+    ring = 16
     bufs = [[torch.empty(g.V, dtype=torch.int32, device=dev) for _ in range(ring)] for g in all_g]
     torch.cuda.synchronize()
     budget = 32 * 700_000_000              # label pool of 700M labels (22.4 GB)
@@ -346,6 +347,50 @@ def _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_
             "burst_qps": burst_qps, "rates": rates, "server": stats,
             "budget_bytes": budget, "slots": 512,
             "latency": "host steady clock, submission to completion observed by the server"}
+
+
+def queue_leg(dev, n_ops=10_000_000):
+    """The paper's queue workloads (Sec. IV): EnqDeq (n enqueues, then n
+    dequeues) and Mixed (even blocks enqueue n/2 while odd blocks dequeue n/2)
+    for the per-thread Broker Queue, the Broker Work Distributor and the
+    warp-aggregated Broker Queue, over a few launch shapes; best ops/s kept."""
+    import torch
+    from paper_2608_21826_gb300 import bfq
+    items = torch.arange(n_ops, dtype=torch.int32, device=dev)
+    out = torch.empty(n_ops, dtype=torch.int32, device=dev)
+    shapes = [(108, 256), (216, 512), (152 * 8, 256)]
+    res = {}
+    for name, var in (("bq", bfq.QUEUE_BQ), ("bwd", bfq.QUEUE_BWD), ("bq_warp", bfq.QUEUE_BQ_WARP)):
+        q = bfq.bfq_queue_create(n_ops, var)
+        best = {}
+        try:
+            for grid, block in shapes:
+                for kind in ("enqdeq", "mixed"):
+                    bfq.bfq_queue_reset(q)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    if kind == "enqdeq":
+                        bfq.bfq_queue_enqueue(q, items, None, grid, block)
+                        bfq.bfq_queue_dequeue(q, out, None, grid, block)
+                    else:
+                        bfq.bfq_queue_mixed(q, items[: n_ops // 2], out[: n_ops // 2], None, None,
+                                            grid, block)
+                    e1.record()
+                    e1.synchronize()
+                    st, head, tail, count = bfq.bfq_queue_state(q)
+                    ms = e0.elapsed_time(e1)
+                    ops = 2 * n_ops if kind == "enqdeq" else n_ops
+                    rate = ops / (ms / 1e3)
+                    if st == bfq.OK and (kind not in best or rate > best[kind]["ops_per_s"]):
+                        best[kind] = {"ops_per_s": rate, "ms": ms, "grid": grid, "block": block,
+                                      "dequeued": int(head)}
+        finally:
+            bfq.bfq_queue_destroy(q)
+        res[name] = best
+    return {"ops": n_ops, "variants": res,
+            "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts"}
 
 
 def run_reference(args):
@@ -495,6 +540,12 @@ def run_ours(args):
             batched = {"error": repr(e)}
         for hh in bhandles:
             bfq.bfq_graph_destroy(hh)
+    queue = None
+    if not args.no_queue:
+        try:
+            queue = queue_leg(dev)
+        except Exception as e:
+            queue = {"error": repr(e)}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(g, 1)
@@ -522,6 +573,7 @@ def run_ours(args):
         "clocks": clk,
         "batched": batched,
         "serve": serve,
+        "queue": queue,
     }
     print(json.dumps(line), flush=True)
 

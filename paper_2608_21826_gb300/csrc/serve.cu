@@ -47,7 +47,7 @@ int graph_view(bfq_graph_t g, GraphView* out);
 namespace {
 
 constexpr int kPageLog2 = 12;            // label pool page: 4096 labels
-constexpr int kTaskLog2 = 16;            // init / unpack task: 65536 labels
+constexpr int kTaskLog2 = 14;            // init / unpack task: 16384 labels
 constexpr int kChunkIdBits = 20;         // chunk item = slot << 20 | chunk
 constexpr int kMaxSlots = 2048;          // 11 bits of slot in task items
 
@@ -192,7 +192,7 @@ __device__ __forceinline__ bool admit_one(const ServeArgs& a, int lane) {
   return true;
 }
 
-// Init task: labels of [t * 65536, ...) of the slot to infinity (the source
+// Init task: labels of [t * 16384, ...) of the slot to infinity (the source
 // to (0, 0), queued), page owners; the last one queues the source.
 // Unpack task: dist / hops out; the last one posts the completion.
 __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int lane, int home) {
@@ -218,11 +218,19 @@ __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int la
     const int p0 = (d.label_off + lo) >> kPageLog2, p1 = (d.label_off + hi - 1) >> kPageLog2;
     for (int p = p0 + lane; p <= p1; p += 32) a.page_owner[p] = slot;
   } else if (d.dist || d.hops) {
-    for (int i = lo + lane; i < hi; i += 32) {
-      const long long l = lab[i];
-      const int dd = label_dist(l);
-      if (d.dist) d.dist[i] = dd;
-      if (d.hops) d.hops[i] = (dd == kInf32) ? -1 : (int)label_hops(l);
+    // eight labels in flight per lane
+    for (int i0 = lo + lane; i0 < hi; i0 += 32 * 8) {
+      long long l[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) l[k] = (i0 + 32 * k < hi) ? lab[i0 + 32 * k] : 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = i0 + 32 * k;
+        if (i >= hi) break;
+        const int dd = label_dist(l[k]);
+        if (d.dist) d.dist[i] = dd;
+        if (d.hops) d.hops[i] = (dd == kInf32) ? -1 : (int)label_hops(l[k]);
+      }
     }
   }
   __syncwarp();
@@ -279,7 +287,14 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
   int idle = 0;
   bool failed = false;
 
+  int since_admit = 0;
   for (;;) {
+    // 0) busy warps also take admissions now and then, so that arrivals do
+    // not wait for the device to run dry
+    if (++since_admit >= 16) {
+      since_admit = 0;
+      if (admit_one(a, lane)) idle = 0;
+    }
     // 1) init / unpack tasks
     unsigned item = 0;
     int c = 0;
@@ -336,13 +351,20 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
       // 3) admission, then idle
       if (admit_one(a, lane)) { idle = 0; continue; }
       if (idle == 0) t_idle = globaltimer_ns();
+      // leaving is decided for the whole launch (a warp sets the stop flag,
+      // every warp follows), so the kernel never lingers with a few warps
       int leave = 0;
       if (lane == 0) {
         const unsigned long long now = globaltimer_ns();
-        if (ld_relaxed_s32(&a.ctl->stop) || ld_acquire_sys_s32(a.shutdown)) leave = 1;
-        else if ((long long)(now - t_start) > a.time_limit_ns) leave = 1;
-        else if (ld_relaxed_s32(&a.ctl->active) == 0 &&
-                 (long long)(now - t_idle) > a.idle_exit_ns) leave = 1;
+        if (ld_relaxed_s32(&a.ctl->stop)) {
+          leave = 1;
+        } else if (ld_acquire_sys_s32(a.shutdown) ||
+                   (long long)(now - t_start) > a.time_limit_ns ||
+                   (ld_relaxed_s32(&a.ctl->active) == 0 &&
+                    (long long)(now - t_idle) > a.idle_exit_ns)) {
+          st_relaxed_s32(&a.ctl->stop, 1);
+          leave = 1;
+        }
       }
       if (__shfl_sync(kFullMask, leave, 0)) break;
       ++wc.idle;
@@ -764,6 +786,7 @@ struct bfq_server {
       }
       if (!launched && !admitted.empty() && !stopping) {
         completed_at_launch = completed;
+        cudaMemsetAsync(&args.ctl->stop, 0, sizeof(int), stream);
         serve_kernel<<<grid, kBlock, 0, stream>>>(args);
         cudaEventRecord(kernel_done, stream);
         launched = true;
