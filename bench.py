@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-queue", action="store_true")
+    p.add_argument("--no-rounds", action="store_true")
+    p.add_argument("--no-l2", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
     return p.parse_args()
@@ -393,6 +395,72 @@ def queue_leg(dev, n_ops=10_000_000):
             "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts"}
 
 
+def rounds_leg(h, srcs, dist_t, flush, stream, m_per_query, queue_kernel_ms):
+    """The round-based formulation (change-counter rounds, Algorithm 3) on the
+    same resident graph and sources, beside the queue-driven kernel: device
+    time of the round kernel per query, rounds, edges relaxed.  Each mode's
+    first query is a warm-up (it also builds the per-edge tail array)."""
+    import torch
+    from paper_2608_21826_gb300 import bfq
+    out = {}
+    for name, flags in (("changed_tails", 0), ("all_edges", bfq.ROUNDS_ALL_EDGES)):
+        bfq.bfq_sssp_rounds(h, srcs[0], dist_t, flags=flags)
+        ms, rounds, relaxed, total = [], [], [], []
+        for i, s in enumerate(srcs):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, stt = bfq.bfq_sssp_rounds(h, s, dist_t, flags=flags, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if st != bfq.OK:
+                raise RuntimeError(f"rounds query status {st}")
+            ms.append(stt["kernel_ms"])
+            total.append(e0.elapsed_time(e1))
+            rounds.append(stt["rounds"])
+            relaxed.append(stt["relaxed"])
+        k = sum(ms) / len(ms)
+        out[name] = {"kernel_ms_per_query": k, "call_ms_per_query": sum(total) / len(total),
+                     "gteps": m_per_query / (k / 1e3) / 1e9,
+                     "rounds_per_query": sum(rounds) / len(rounds),
+                     "relaxed_per_query": sum(relaxed) / len(relaxed),
+                     "work_ratio": sum(relaxed) / len(relaxed) / max(1.0, m_per_query)}
+    out["queue_kernel_ms_per_query"] = queue_kernel_ms
+    out["queue_speedup_vs_changed_tails"] = out["changed_tails"]["kernel_ms_per_query"] / queue_kernel_ms
+    return out
+
+
+def l2_leg(h, srcs, dist_t, status, flush, stream, pcts=(0, 25, 50, 75, 100)):
+    """Persisting-L2 window over the label array: kernel time per query for
+    each set-aside share (the L2 flush between queries does not evict
+    persisting lines, which is the point of the window)."""
+    import torch
+    from paper_2608_21826_gb300 import bfq
+    base = bfq.bfq_graph_get_tune(h)
+    out = {}
+    try:
+        for pct in pcts:
+            t = bfq.bfq_graph_get_tune(h)
+            t.l2_persist_pct = pct
+            bfq.bfq_graph_set_tune(h, t)
+            bfq.bfq_sssp(h, srcs[0], dist_t)
+            ms = []
+            for rep in range(2):
+                for i, s in enumerate(srcs):
+                    flush.fill_(i & 0xFF)
+                    bfq.bfq_sssp_async(h, s, dist_t, None, None, status[i:i + 1], stream)
+                    stream.synchronize()
+                    ms.append(bfq.bfq_get_stats(h)["kernel_ms"])
+            if any(x != bfq.OK for x in status.cpu().tolist()):
+                raise RuntimeError("l2 leg: a query did not finish cleanly")
+            out[str(pct)] = sum(ms) / len(ms)
+    finally:
+        bfq.bfq_graph_set_tune(h, base)
+    return {"kernel_ms_per_query_by_pct": out,
+            "window": "label array (8 B/vertex), hitRatio = set-aside / window"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -444,6 +512,11 @@ def run_ours(args):
     status = torch.zeros(len(srcs), dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    # run-time parameters picked by the library's autotuner (untimed)
+    tuned = bfq.bfq_autotune(h, srcs)
+    tune_desc = {"share_div": tuned.share_div, "chunk_batch": tuned.chunk_batch,
+                 "batch_items": tuned.batch_items}
 
     def one_step(record):
         """4 queries; returns per-query (device ms, stats)."""
@@ -522,6 +595,18 @@ def run_ours(args):
                "note": "bfq_sssp (host-synchronous) per source + copy of dist to pinned host; "
                        "sources pass by value, the graph is resident"}
 
+    rounds = l2 = None
+    if rank == 0 and not args.no_rounds:
+        try:
+            rounds = rounds_leg(h, srcs, dist_t, flush, stream, m_reached / n_q,
+                                sum(k_ms) / n_q)
+        except Exception as e:                               # reported, not fatal
+            rounds = {"error": repr(e)}
+    if rank == 0 and not args.no_l2:
+        try:
+            l2 = l2_leg(h, srcs, dist_t, status, flush, stream)
+        except Exception as e:
+            l2 = {"error": repr(e)}
     bfq.bfq_graph_destroy(h)
     if rank != 0:
         return
@@ -555,7 +640,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "V": V, "E": g.E,
-                   "queries_per_step": len(srcs),
+                   "queries_per_step": len(srcs), "tune": tune_desc,
                    "l2": "flushed before each query (256 MiB write, untimed)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -574,6 +659,8 @@ def run_ours(args):
         "batched": batched,
         "serve": serve,
         "queue": queue,
+        "rounds": rounds,
+        "l2_window": l2,
     }
     print(json.dumps(line), flush=True)
 

@@ -183,6 +183,54 @@ int bfq_get_stats(bfq_graph_t g, bfq_stats* out);
  * before any stream capture.  Every call reuses the same array and clears
  * the parts it needs, so calls whose GPU work overlaps (on two streams, or
  * from two threads) race and must be serialised by the caller. */
+/* ---- round-based Bellman-Ford (Algorithm 3's formulation, Sec. III-C) ---
+ * Algorithm 3 relaxes the edge list in synchronous rounds, counts the label
+ * decreases of each round in a change counter, stops after a round with no
+ * change, and reports a negative cycle when round V still changes a label.
+ * bfq_sssp_rounds runs that formulation on one GPU, on the same graph handle
+ * and with the same packed (dist, hops) labels as bfq_sssp, so dist, hops and
+ * pred are identical to bfq_sssp's for every graph without a reachable
+ * negative cycle.  A label of V or more hops also proves a negative cycle and
+ * usually ends such runs long before round V.  By default a round relaxes
+ * only the edges whose tail changed in the previous round (the fixed point
+ * is the same); BFQ_ROUNDS_ALL_EDGES relaxes every edge every round, as the
+ * algorithm prints it.  The first call on a handle adds 4 B per edge plus
+ * 12 B per 32 vertices of workspace (counted by bfq_graph_device_bytes).
+ * Runs as one cooperative launch; synchronises `stream`.
+ *   dist: int32[V] device (required); hops, pred: int32[V] device or NULL;
+ *   stats: host struct or NULL.
+ * Returns BFQ_OK, BFQ_NEG_CYCLE, BFQ_RANGE, BFQ_ERR_TIMEOUT (a grid barrier
+ * waited longer than spin_limit polls, or the run longer than time_limit_ms)
+ * or an argument/CUDA error.  After BFQ_NEG_CYCLE, BFQ_RANGE or a timeout
+ * dist/hops hold the labels reached and pred is all -1. */
+#define BFQ_ROUNDS_ALL_EDGES 1
+
+typedef struct bfq_rounds_stats {
+  int64_t rounds;     /* rounds run, the last one included                  */
+  int64_t relaxed;    /* edges relaxed over all rounds                      */
+  int64_t updated;    /* label decreases: the sum of the change counters    */
+  double kernel_ms;   /* device time of the round kernel (CUDA events)      */
+  int64_t reserved[4];
+} bfq_rounds_stats;
+
+int bfq_sssp_rounds(bfq_graph_t g, int32_t src, int32_t flags, int32_t* dist,
+                    int32_t* hops, int32_t* pred, bfq_rounds_stats* stats,
+                    void* stream);
+
+/* Run-time parameters of a graph handle.  set_tune validates like
+ * bfq_graph_create (zero fields take the defaults) and rejects a change of
+ * the parameters that size the workspace (threads_per_cta, ctas_per_sm,
+ * queues_per_cta, hub_degree, chunk_edges) with BFQ_ERR_INVALID; the others
+ * take effect at the next query.  A non-zero l2_persist_pct sets aside that
+ * share of the device's maximum persisting L2 for the calling context
+ * (cudaLimitPersistingL2CacheSize) and attaches an access-policy window over
+ * the label array to the persistent launch.  Setting it back to 0, or
+ * destroying the handle, drops the persisting lines and restores the
+ * context's previous persisting-L2 limit (the set-aside takes L2 capacity
+ * from every other kernel of the process while it is held). */
+int bfq_graph_get_tune(bfq_graph_t g, bfq_tune* out);
+int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
+
 int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
                      int64_t E, int32_t src, int32_t* dist, int32_t* hops,
                      int32_t* status_dev, void* stream);

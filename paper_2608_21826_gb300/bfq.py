@@ -50,6 +50,14 @@ class Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int64 * 4)]
 
 
+class RoundsStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("relaxed", ctypes.c_int64),
+                ("updated", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+ROUNDS_ALL_EDGES = 1
+
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -65,6 +73,10 @@ _SIGNATURES = {
     "bfq_sssp_async": ([_VP, _I32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "bfq_get_stats": ([_VP, ctypes.POINTER(Stats)], ctypes.c_int),
     "bfq_sssp_noalloc": ([_VP, _VP, _I32, _I64, _I32, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "bfq_sssp_rounds": ([_VP, _I32, _I32, _VP, _VP, _VP, ctypes.POINTER(RoundsStats), _VP],
+                        ctypes.c_int),
+    "bfq_graph_get_tune": ([_VP, ctypes.POINTER(Tune)], ctypes.c_int),
+    "bfq_graph_set_tune": ([_VP, ctypes.POINTER(Tune)], ctypes.c_int),
     "bfq_autotune": ([_VP, _VP, _I32, ctypes.POINTER(Tune), _VP], ctypes.c_int),
     "bfq_batch_create": ([ctypes.POINTER(_VP), _VP, _I32, _I32, _I64, ctypes.POINTER(Tune)],
                          ctypes.c_int),
@@ -217,6 +229,25 @@ def bfq_get_stats(g) -> dict:
     s = Stats()
     _check(lib().bfq_get_stats(g, ctypes.byref(s)))
     return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+
+
+def bfq_sssp_rounds(g, src: int, dist, hops=None, pred=None, flags: int = 0,
+                    stream=None) -> tuple[int, dict]:
+    """Round-based query (change-counter rounds); returns (status, stats)."""
+    st = RoundsStats()
+    rc = _check(lib().bfq_sssp_rounds(g, int(src), int(flags), _ptr(dist), _ptr(hops),
+                                      _ptr(pred), ctypes.byref(st), _stream(stream)))
+    return rc, {name: getattr(st, name) for name, _ in RoundsStats._fields_ if name != "reserved"}
+
+
+def bfq_graph_get_tune(g) -> Tune:
+    t = Tune()
+    _check(lib().bfq_graph_get_tune(g, ctypes.byref(t)))
+    return t
+
+
+def bfq_graph_set_tune(g, tune: Tune) -> None:
+    _check(lib().bfq_graph_set_tune(g, ctypes.byref(tune)))
 
 
 def bfq_sssp_noalloc(row_ptr, adj, V: int, E: int, src: int, dist, hops=None, status_dev=None,
@@ -410,6 +441,16 @@ class Graph:
             dist = torch.empty(self.V, dtype=torch.int32, device=dev)
         st = bfq_sssp(self.handle, src, dist, hops, pred, stream)
         return st, dist, hops, pred
+
+    def sssp_rounds(self, src: int, dist=None, hops=None, pred=None, flags: int = 0,
+                    stream=None):
+        """Round-based query; returns (status, dist, stats)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty(self.V, dtype=torch.int32, device=dev)
+        st, stats = bfq_sssp_rounds(self.handle, src, dist, hops, pred, flags, stream)
+        return st, dist, stats
 
     def stats(self) -> dict:
         return bfq_get_stats(self.handle)

@@ -71,9 +71,10 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 // Kernels launchers (sssp.cu)
 int sssp_max_ctas_per_sm(int block);
 // init, persistent run (bracketed by ev0/ev1 when given), epilogue, pred.
+// l2win (nullable): L2 access-policy window attached to the persistent launch.
 cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,
                         int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
-                        cudaStream_t s);
+                        cudaStream_t s, const cudaAccessPolicyWindow* l2win = nullptr);
 cudaError_t launch_reached_edges(const int* row_ptr, const long long* label, int V,
                                  unsigned long long* out2, cudaStream_t s);
 cudaError_t launch_pack_adj(const int* col, const int* w, int2* adj, long long E, cudaStream_t s);
@@ -87,5 +88,36 @@ cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape
 // status code; `bad` (nullable, device) forces BFQ_ERR_INVALID when non-zero.
 cudaError_t launch_sssp_epilogue(const SsspArgs& a, LaunchShape shape, int32_t* status_dev,
                                  const int* bad, cudaStream_t s);
+
+// Predecessor pass alone over final labels (pred must hold -1 beforehand).
+cudaError_t launch_pred_pass(const int* row_ptr, const int2* adj, const long long* label, int V,
+                             int* pred, cudaStream_t s);
+
+// Round-based relaxation (rounds.cu).  Workspace made on first use.
+struct RoundsState {
+  int* tail = nullptr;          // [E] tail vertex of each edge
+  int2* chunk_rng = nullptr;    // first and last tail of each edge chunk
+  unsigned* bits = nullptr;     // three changed-vertex bitmaps
+  void* ctl = nullptr;          // device counters
+  void* host = nullptr;         // pinned copy of the counters
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int grid = 0;
+  RoundsState() = default;
+  RoundsState(const RoundsState&) = delete;
+  RoundsState& operator=(const RoundsState&) = delete;
+  ~RoundsState();
+};
+struct RoundsResult {
+  long long rounds;
+  long long relaxed;
+  long long updated;
+  float kernel_ms;
+};
+long long rounds_device_bytes(int V, long long E);
+// Runs one query and synchronises `s`; returns a BFQ_* status code.
+int rounds_run(RoundsState& st, const int* row_ptr, const int2* adj, long long* label, int V,
+               long long E, int src, int flags, int* dist, int* hops, int* pred,
+               long long spin_limit, long long time_limit_ms, RoundsResult* res,
+               cudaStream_t s);
 
 }  // namespace bfq

@@ -62,6 +62,10 @@ struct bfq_graph {
   long long bytes = 0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the persistent kernel
+  int l2_pct_applied = 0;                      // l2_persist_pct the window was made for
+  size_t l2_limit_saved = 0;                   // persisting-L2 limit before the first window
+  cudaAccessPolicyWindow l2win{};
+  RoundsState rounds;                          // round-based path, made on first use
   std::vector<void*> allocs;
 
   int alloc(void** p, size_t n) {
@@ -72,7 +76,16 @@ struct bfq_graph {
     bytes += (long long)n;
     return BFQ_OK;
   }
+  // Drop this handle's persisting lines and give the context its previous
+  // persisting-L2 limit back.
+  void release_l2() {
+    if (l2_pct_applied == 0) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, l2_limit_saved);
+    l2_pct_applied = 0;
+  }
   ~bfq_graph() {
+    release_l2();
     for (void* p : allocs) cudaFree(p);
     if (status_host) cudaFreeHost(status_host);
     if (ev0) cudaEventDestroy(ev0);
@@ -331,6 +344,36 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   return a;
 }
 
+// L2 persistence for the label array (Sec. IV's L2 set-aside sweep): set
+// aside l2_persist_pct percent of the device's maximum persisting L2 for this
+// context and describe a window over the labels, attached to the persistent
+// launch.  The set-aside is a limit of the calling process's context; the
+// previous limit comes back when the share returns to 0 or the handle goes.
+static int apply_l2_window(bfq_graph_t g) {
+  const int pct = g->tune.l2_persist_pct;
+  if (g->l2_pct_applied == pct) return BFQ_OK;
+  int max_persist = 0, max_window = 0;
+  BFQ_CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize,
+                                      g->device));
+  BFQ_CUDA_TRY(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize,
+                                      g->device));
+  if (max_persist <= 0 || max_window <= 0)
+    return invalid("bfq_sssp: the device offers no persisting L2 (l2_persist_pct must be 0)");
+  if (g->l2_pct_applied == 0)
+    BFQ_CUDA_TRY(cudaDeviceGetLimit(&g->l2_limit_saved, cudaLimitPersistingL2CacheSize));
+  const size_t setaside = (size_t)max_persist * (size_t)pct / 100;
+  BFQ_CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, setaside));
+  const size_t bytes = std::min(sizeof(long long) * (size_t)g->V, (size_t)max_window);
+  g->l2win = cudaAccessPolicyWindow{};
+  g->l2win.base_ptr = g->label;
+  g->l2win.num_bytes = bytes;
+  g->l2win.hitRatio = std::min(1.0f, (float)setaside / (float)bytes);
+  g->l2win.hitProp = cudaAccessPropertyPersisting;
+  g->l2win.missProp = cudaAccessPropertyStreaming;
+  g->l2_pct_applied = pct;
+  return BFQ_OK;
+}
+
 int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* pred,
                    int32_t* status_dev, void* stream) {
   if (!g) return invalid("bfq_sssp: null graph handle");
@@ -338,8 +381,16 @@ int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int
   if (!dist) return invalid("bfq_sssp: dist is null");
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
+  const cudaAccessPolicyWindow* win = nullptr;
+  if (g->tune.l2_persist_pct > 0) {
+    const int rc = apply_l2_window(g);
+    if (rc != BFQ_OK) return rc;
+    win = &g->l2win;
+  } else {
+    g->release_l2();
+  }
   SsspArgs a = make_args(g, src, dist, hops, pred);
-  BFQ_CUDA_TRY(launch_sssp(a, g->init_shape, g->run_shape, status_dev, g->ev0, g->ev1, s));
+  BFQ_CUDA_TRY(launch_sssp(a, g->init_shape, g->run_shape, status_dev, g->ev0, g->ev1, s, win));
   return BFQ_OK;
 }
 
@@ -354,6 +405,52 @@ int bfq_sssp(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* 
   const int st = *g->status_host;
   if (st == BFQ_ERR_TIMEOUT) set_error("bfq_sssp: a bounded device-side wait ran out");
   return st;
+}
+
+int bfq_sssp_rounds(bfq_graph_t g, int32_t src, int32_t flags, int32_t* dist, int32_t* hops,
+                    int32_t* pred, bfq_rounds_stats* stats, void* stream) {
+  if (!g) return invalid("bfq_sssp_rounds: null graph handle");
+  if (src < 0 || src >= g->V) return invalid("bfq_sssp_rounds: source out of range");
+  if (!dist) return invalid("bfq_sssp_rounds: dist is null");
+  if (flags & ~BFQ_ROUNDS_ALL_EDGES) return invalid("bfq_sssp_rounds: unknown flag");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fresh = g->rounds.grid == 0;
+  RoundsResult r{};
+  const int rc = rounds_run(g->rounds, g->row_ptr, g->adj, g->label, g->V, g->E, src, flags, dist,
+                            hops, pred, g->tune.spin_limit, g->tune.time_limit_ms, &r, s);
+  if (fresh && g->rounds.grid != 0) g->bytes += rounds_device_bytes(g->V, g->E);
+  if (rc < 0 && rc != BFQ_ERR_TIMEOUT) return rc;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->rounds = r.rounds;
+    stats->relaxed = r.relaxed;
+    stats->updated = r.updated;
+    stats->kernel_ms = r.kernel_ms;
+  }
+  return rc;
+}
+
+int bfq_graph_get_tune(bfq_graph_t g, bfq_tune* out) {
+  if (!g || !out) return invalid("bfq_graph_get_tune: null argument");
+  *out = g->tune;
+  return BFQ_OK;
+}
+
+int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t) {
+  if (!g || !t) return invalid("bfq_graph_set_tune: null argument");
+  bfq_tune n{};
+  const int rc = fill_tune(t, &n);
+  if (rc != BFQ_OK) return rc;
+  const bfq_tune& o = g->tune;
+  if (n.threads_per_cta != o.threads_per_cta || n.queues_per_cta != o.queues_per_cta ||
+      n.hub_degree != o.hub_degree || n.chunk_edges != o.chunk_edges ||
+      (t->ctas_per_sm != 0 && t->ctas_per_sm != o.ctas_per_sm))
+    return invalid("bfq_graph_set_tune: threads_per_cta, ctas_per_sm, queues_per_cta, "
+                   "hub_degree and chunk_edges are fixed when the graph is created");
+  n.ctas_per_sm = o.ctas_per_sm;
+  g->tune = n;
+  if (n.l2_persist_pct == 0) g->release_l2();
+  return BFQ_OK;
 }
 
 int bfq_get_stats(bfq_graph_t g, bfq_stats* out) {

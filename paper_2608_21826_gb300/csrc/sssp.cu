@@ -401,7 +401,7 @@ __global__ void sssp_init_kernel(SsspArgs a) {
 __global__ void sssp_pred_kernel(const int* __restrict__ row_ptr, const int2* __restrict__ adj,
                                  const long long* __restrict__ label, int V, int* pred,
                                  const Control* ctl) {
-  if (ctl->last_status != 0) return;
+  if (ctl && ctl->last_status != 0) return;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -480,15 +480,35 @@ int sssp_max_ctas_per_sm(int block) {
 
 cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,
                         int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
-                        cudaStream_t s) {
+                        cudaStream_t s, const cudaAccessPolicyWindow* l2win) {
   sssp_init_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a);
   if (ev0) cudaEventRecord(ev0, s);
-  sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  if (l2win) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(run_shape.grid);
+    cfg.blockDim = dim3(run_shape.block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *l2win;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, sssp_persistent_kernel, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  }
   if (ev1) cudaEventRecord(ev1, s);
   sssp_epilogue_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a, status_dev, nullptr);
   if (a.pred)
     sssp_pred_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a.row_ptr, a.adj, a.label, a.V,
                                                                  a.pred, a.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_pass(const int* row_ptr, const int2* adj, const long long* label, int V,
+                             int* pred, cudaStream_t s) {
+  sssp_pred_kernel<<<1024, 256, 0, s>>>(row_ptr, adj, label, V, pred, nullptr);
   return cudaGetLastError();
 }
 
