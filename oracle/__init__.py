@@ -5,7 +5,8 @@ legs of ``bench.py`` may import this package.  The library under
 ``paper_2608_21826_gb300`` never imports it and shares no code with it.
 
 ``sssp_oracle.c`` holds the plain sequential algorithms (FIFO label-correcting
-Bellman-Ford, Dijkstra, Floyd-Warshall, the predecessor-tree invariant).  This
+Bellman-Ford, Dijkstra, Floyd-Warshall, the predecessor-tree invariant, and
+distances with negative cycles resolved to minus infinity).  This
 module compiles it with gcc on first use (or from ``build()``) and exposes thin
 numpy wrappers.  ``broker_queue.py`` models the Broker Queue of Algorithm 1.
 """
@@ -52,6 +53,8 @@ def _bind(lib):
         f = getattr(lib, name)
         f.argtypes = [i32, p32, p32, p32, i32, p32, p32]
         f.restype = ctypes.c_int
+    lib.oracle_spfa_neg_inf.argtypes = [i32, p32, p32, p32, i32, p32, p32]
+    lib.oracle_spfa_neg_inf.restype = ctypes.c_int
     lib.oracle_check_pred.argtypes = [i32, p32, p32, p32, i32, p32, p32]
     lib.oracle_check_pred.restype = ctypes.c_int
     lib.oracle_reached_edges.argtypes = [i32, p32, p32]
@@ -79,6 +82,9 @@ class Variant:
 
     def dijkstra(self, *a):
         return dijkstra(*a, _lib=self._lib)
+
+    def spfa_neg_inf(self, *a):
+        return spfa_neg_inf(*a, _lib=self._lib)
 
     def floyd_warshall(self, *a):
         return floyd_warshall(*a, _lib=self._lib)
@@ -111,6 +117,24 @@ def spfa(row_ptr, col, w, src: int, _lib=None):
     if st < 0:
         raise ValueError(f"oracle_spfa rejected its input ({st})")
     return st, dist, hops, scanned.value
+
+
+NEG_INF_DIST = -2147483648      # dist of a vertex reachable from a negative cycle
+NEG_INF_HOPS = -2
+
+
+def spfa_neg_inf(row_ptr, col, w, src: int, _lib=None):
+    """Distances with negative cycles resolved: vertices reachable from a
+    reachable negative cycle get (INT32_MIN, -2), the others their
+    lexicographic labels.  Returns (status, dist, hops)."""
+    V, row_ptr, col, w = _csr(row_ptr, col, w)
+    dist = np.empty(V, np.int32)
+    hops = np.empty(V, np.int32)
+    st = (_lib or _load()).oracle_spfa_neg_inf(V, _p(row_ptr), _p(col), _p(w), int(src),
+                                               _p(dist), _p(hops))
+    if st < 0:
+        raise ValueError(f"oracle_spfa_neg_inf rejected its input ({st})")
+    return st, dist, hops
 
 
 def dijkstra(row_ptr, col, w, src: int, _lib=None):

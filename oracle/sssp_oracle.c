@@ -124,6 +124,99 @@ int oracle_spfa(int32_t V, const int32_t* row_ptr, const int32_t* col,
 }
 
 /*
+ * Distances with negative cycles resolved.  The paper stops at reporting that
+ * a negative cycle is reachable; this states the usual refinement of that
+ * answer, which the library offers as an option: d(v) = -infinity exactly
+ * when some vertex of a negative cycle reachable from s reaches v (walks to v
+ * are then unboundedly short); every other reachable v keeps its
+ * lexicographic (dist, hops) label, all of whose walks avoid the -infinity
+ * vertices.  Steps:
+ *   1. Bellman-Ford rounds from s in int64, each round reading the previous
+ *      round's distances (Jacobi form), V-1 rounds at most, stopping early
+ *      after a round without change.  After round k every d[v] is the least
+ *      weight over s->v walks of at most k edges.
+ *   2. One further round: the head of every edge (u, v) with u reached and
+ *      d[u] + w < d[v] is marked.  Each reachable negative cycle has such an
+ *      edge (the inequalities cannot all fail around a cycle of negative
+ *      weight), and a marked head is reachable from a negative cycle (without
+ *      one, d[u] and d[v] are final after V-1 rounds and the test fails).
+ *   3. Every vertex reachable from a marked vertex is -infinity.
+ *   4. oracle_spfa on the graph without the -infinity vertices' edges gives
+ *      the other labels (status OK or RANGE there).
+ * Output: dist INT32_MIN and hops -2 on -infinity vertices, dist INT32_MAX
+ * and hops -1 on unreachable ones.  Status NEG_CYCLE when a vertex is
+ * -infinity, else the status of step 4.
+ */
+int oracle_spfa_neg_inf(int32_t V, const int32_t* row_ptr, const int32_t* col,
+                        const int32_t* w, int32_t src, int32_t* dist, int32_t* hops) {
+  if (!check_csr(V, row_ptr, col, src)) return ORC_ERR_INVALID;
+  const int64_t E = row_ptr[V];
+  const int64_t INF64 = INT64_MAX;
+  int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  int64_t* dn = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  char* ninf = (char*)calloc((size_t)V, 1);
+  int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)V);
+  int32_t* rp2 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)V + 1));
+  int32_t* col2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+  int32_t* w2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+  if (!d || !dn || !ninf || !stack || !rp2 || !col2 || !w2) {
+    free(d); free(dn); free(ninf); free(stack); free(rp2); free(col2); free(w2);
+    return ORC_ERR_OOM;
+  }
+  /* 1. Jacobi Bellman-Ford rounds */
+  for (int32_t v = 0; v < V; ++v) d[v] = INF64;
+  d[src] = 0;
+  int changed = 1;
+  for (int64_t round = 1; round <= (int64_t)V - 1 && changed; ++round) {
+    changed = 0;
+    memcpy(dn, d, sizeof(int64_t) * (size_t)V);
+    for (int32_t u = 0; u < V; ++u) {
+      if (d[u] == INF64) continue;
+      for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+        const int64_t nd = d[u] + (int64_t)w[e];
+        if (nd < dn[col[e]]) { dn[col[e]] = nd; changed = 1; }
+      }
+    }
+    memcpy(d, dn, sizeof(int64_t) * (size_t)V);
+  }
+  /* 2. heads of edges still relaxable; 3. everything they reach */
+  int64_t top = 0;
+  if (changed) {
+    for (int32_t u = 0; u < V; ++u) {
+      if (d[u] == INF64) continue;
+      for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+        const int32_t v = col[e];
+        if (d[u] + (int64_t)w[e] < d[v] && !ninf[v]) { ninf[v] = 1; stack[top++] = v; }
+      }
+    }
+  }
+  while (top > 0) {
+    const int32_t u = stack[--top];
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+      const int32_t v = col[e];
+      if (!ninf[v]) { ninf[v] = 1; stack[top++] = v; }
+    }
+  }
+  /* 4. labels of the rest on the graph without the -infinity vertices' edges */
+  int64_t k = 0;
+  int any = 0;
+  rp2[0] = 0;
+  for (int32_t u = 0; u < V; ++u) {
+    any |= ninf[u];
+    if (!ninf[u])
+      for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+        if (!ninf[col[e]]) { col2[k] = col[e]; w2[k] = w[e]; ++k; }
+    rp2[u + 1] = (int32_t)k;
+  }
+  int status = oracle_spfa(V, rp2, col2, w2, src, dist, hops, NULL);
+  for (int32_t v = 0; v < V; ++v)
+    if (ninf[v]) { dist[v] = (int32_t)ORC_MIN32; hops[v] = -2; }
+  if (status >= 0 && any) status = ORC_NEG_CYCLE;
+  free(d); free(dn); free(ninf); free(stack); free(rp2); free(col2); free(w2);
+  return status;
+}
+
+/*
  * Dijkstra with a binary heap on lexicographic (dist, hops) keys.  Requires
  * every weight >= 0.  Used to pin the SPFA oracle through the potential
  * transform: if w'(u,v) = w(u,v) + p(u) - p(v) then every s->v path changes

@@ -13,8 +13,11 @@ GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 INF = 2147483647
 
 
+NEG_INF = -2147483648
+
+
 def _ints(tokens):
-    return [INF if t == "INF" else int(t) for t in tokens]
+    return [INF if t == "INF" else NEG_INF if t == "NEGINF" else int(t) for t in tokens]
 
 
 def load_golden(path):
@@ -43,6 +46,10 @@ def load_golden(path):
 
 def golden_files():
     return sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))
+
+
+def golden_neg_inf_files():
+    return sorted(glob.glob(os.path.join(GOLDEN_DIR, "neg_inf", "*.txt")))
 
 
 def brute_force(g, src):
@@ -88,6 +95,63 @@ def brute_force(g, src):
     for v, (d, h) in best.items():
         dist[v], hops[v] = d, h
     return neg, dist, hops
+
+
+def subgraph_without(g, drop):
+    """The same vertices with every edge that touches a vertex in `drop`
+    removed (CSR order kept)."""
+    drop = np.asarray(drop, bool)
+    rp = [0]
+    col, w = [], []
+    for u in range(g.V):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            v = int(g.col[e])
+            if not drop[u] and not drop[v]:
+                col.append(v)
+                w.append(int(g.w[e]))
+        rp.append(len(col))
+    return synth.Graph(g.name + "-sub", np.array(rp, np.int32), np.array(col, np.int32),
+                       np.array(w, np.int32), g.sources)
+
+
+def brute_force_neg_inf(g, src):
+    """Distances with negative cycles resolved, by enumeration (tiny V only):
+    every simple cycle of negative weight through a vertex reachable from
+    src marks its vertices; everything they reach is -inf; the other labels
+    are the lexicographic minimum over simple paths avoiding the -inf
+    vertices.  Returns (any_neg_inf, dist, hops) with (INT32_MIN, -2) on
+    -inf vertices."""
+    V = g.V
+    adj = {u: [] for u in range(V)}
+    for u in range(V):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            adj[u].append((int(g.col[e]), int(g.w[e])))
+    reach = bfs_levels(g, src) >= 0
+    seeds = set()
+
+    def cyc(c, u, d, path):
+        for v, w in adj[u]:
+            if v == c and d + w < 0:
+                seeds.update(path)
+            if v != c and v not in path and v > c:
+                cyc(c, v, d + w, path + [v])
+    for c in range(V):
+        if reach[c]:
+            cyc(c, c, 0, [c])
+    ninf = np.zeros(V, bool)
+    stack = list(seeds)
+    for s in stack:
+        ninf[s] = True
+    while stack:
+        u = stack.pop()
+        for v, _ in adj[u]:
+            if not ninf[v]:
+                ninf[v] = True
+                stack.append(v)
+    _, dist, hops = brute_force(subgraph_without(g, ninf), src)
+    dist[ninf] = NEG_INF
+    hops[ninf] = -2
+    return bool(ninf.any()), dist, hops
 
 
 def bfs_levels(g, src):
