@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-queue", action="store_true")
     p.add_argument("--no-rounds", action="store_true")
     p.add_argument("--no-l2", action="store_true")
+    p.add_argument("--no-neg-inf", action="store_true")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
     return p.parse_args()
@@ -461,6 +462,40 @@ def l2_leg(h, srcs, dist_t, status, flush, stream, pcts=(0, 25, 50, 75, 100)):
             "window": "label array (8 B/vertex), hitRatio = set-aside / window"}
 
 
+def neg_inf_leg(g, dev, reps=3):
+    """The main line's graph with a planted negative 8-cycle reachable from its
+    first source: a query that stops at the first proof of a cycle (the
+    paper's behaviour) beside one that resolves every cycle to minus infinity
+    (neg_cycle_mode MARK); device time of the persistent kernel."""
+    import torch
+    from paper_2608_21826_gb300 import bfq, synth
+    gc = synth.plant_negative_cycle(g, 8, seed=17, reachable_from=[int(g.sources[0])])
+    s = int(g.sources[0])
+    h = bfq.bfq_graph_create(gc.row_ptr, gc.col, gc.w)
+    dist = torch.empty(gc.V, dtype=torch.int32, device=dev)
+    out = {"workload": f"{g.name} + planted negative 8-cycle, source {s}"}
+    try:
+        for name, mode in (("stop", bfq.NEG_CYCLE_STOP), ("mark", bfq.NEG_CYCLE_MARK)):
+            t = bfq.bfq_graph_get_tune(h)
+            t.neg_cycle_mode = mode
+            bfq.bfq_graph_set_tune(h, t)
+            bfq.bfq_sssp(h, s, dist)
+            ms, st = [], None
+            for _ in range(reps):
+                st = bfq.bfq_sssp(h, s, dist)
+                ms.append(bfq.bfq_get_stats(h)["kernel_ms"])
+            ms.sort()
+            row = {"status": st, "kernel_ms": ms[len(ms) // 2]}
+            if mode == bfq.NEG_CYCLE_MARK:
+                row["neg_inf_vertices"] = int((dist == bfq.NEG_INF).sum().item())
+                row["finite_vertices"] = int(((dist != bfq.NEG_INF) &
+                                              (dist != bfq.INF32)).sum().item())
+            out[name] = row
+    finally:
+        bfq.bfq_graph_destroy(h)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -608,6 +643,12 @@ def run_ours(args):
         except Exception as e:
             l2 = {"error": repr(e)}
     bfq.bfq_graph_destroy(h)
+    neg_inf = None
+    if rank == 0 and not args.no_neg_inf:
+        try:
+            neg_inf = neg_inf_leg(g, dev)
+        except Exception as e:
+            neg_inf = {"error": repr(e)}
     if rank != 0:
         return
     batched = serve = None
@@ -661,6 +702,7 @@ def run_ours(args):
         "queue": queue,
         "rounds": rounds,
         "l2_window": l2,
+        "neg_inf": neg_inf,
     }
     print(json.dumps(line), flush=True)
 

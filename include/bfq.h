@@ -99,8 +99,24 @@ typedef struct bfq_tune {
                                of a sub-queue holding count (<= batch_items);
                                0 = the number of warps serving it           */
   int32_t chunk_batch;      /* hub chunks a warp dequeues at once (1..32)    */
-  int32_t reserved[4];
+  int32_t neg_cycle_mode;   /* BFQ_NEG_CYCLE_STOP or BFQ_NEG_CYCLE_MARK, for
+                               bfq_sssp / bfq_sssp_async (see there)         */
+  int32_t reserved[3];
 } bfq_tune;
+
+/* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
+ * reachable negative cycle.  STOP (the paper's behaviour, Sec. III-C: report
+ * only) ends the run at once; dist/hops are then unspecified.  MARK keeps
+ * relaxing and resolves the cycles: every vertex that a reachable negative
+ * cycle reaches gets dist INT32_MIN ("minus infinity") and hops -2, every
+ * other vertex its exact (dist, hops) label and, when asked, a predecessor
+ * (pred -1 on minus-infinity vertices); the status is BFQ_NEG_CYCLE when any
+ * vertex is minus infinity.  The result is unique when V * max|w| < 2^31;
+ * beyond that a falling label may leave the int32 range before its cycle is
+ * proved, and the run reports BFQ_RANGE instead.  The batched, serving,
+ * round-based and allocation-free entry points always STOP. */
+#define BFQ_NEG_CYCLE_STOP 0
+#define BFQ_NEG_CYCLE_MARK 1
 
 /* Counters of the last finished run on a graph handle (summed over warps). */
 typedef struct bfq_stats {

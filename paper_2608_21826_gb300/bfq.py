@@ -35,7 +35,7 @@ class Tune(ctypes.Structure):
                 ("spin_limit", ctypes.c_int64), ("time_limit_ms", ctypes.c_int64),
                 ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("neg_cycle_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -57,6 +57,8 @@ class RoundsStats(ctypes.Structure):
 
 
 ROUNDS_ALL_EDGES = 1
+NEG_CYCLE_STOP, NEG_CYCLE_MARK = 0, 1
+NEG_INF = -2147483648          # dist of a vertex reachable from a negative cycle (MARK)
 
 _VP = ctypes.c_void_p
 _I32 = ctypes.c_int32

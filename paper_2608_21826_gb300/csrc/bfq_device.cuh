@@ -113,6 +113,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // location, so no fence is needed to order the two.
 constexpr long long kQueuedBit = 1LL;
 constexpr long long kInfLabel = 0x7ffffffffffffffeLL;   // (INT32_MAX, 2^31-1), not queued
+// (INT32_MIN, 0): minus infinity, below every other label; only written when
+// negative cycles are resolved (a finite dist never reaches INT32_MIN).
+constexpr long long kNegInfLabel = (long long)0x8000000000000000ULL;
+constexpr int kNegInf32 = (int)0x80000000u;
 
 __device__ __forceinline__ long long pack_label(int dist, unsigned hops) {
   return (long long)(((unsigned long long)(unsigned)dist << 32) |

@@ -51,6 +51,7 @@ struct SsspArgs {
   long long spin_limit;
   long long time_limit_ns;
   int phantom;                  // test hook: unbacked in-flight items
+  int mark_neg_inf;             // 1: resolve negative cycles to minus infinity
 };
 
 struct LaunchShape {

@@ -153,6 +153,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   out->test_phantom_items = in->test_phantom_items;
   if (in->share_div) out->share_div = in->share_div;
   if (in->chunk_batch) out->chunk_batch = in->chunk_batch;
+  out->neg_cycle_mode = in->neg_cycle_mode;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 in this build");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -165,7 +166,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
     return invalid("bfq_tune: hub_degree must be >= chunk_edges");
   if (out->spin_limit < 1 || out->time_limit_ms < 1 || out->ctas_per_sm < 0 ||
       out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0 ||
-      out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32)
+      out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32 ||
+      (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK))
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -341,6 +343,7 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.spin_limit = g->tune.spin_limit;
   a.time_limit_ns = g->tune.time_limit_ms * 1000000LL;
   a.phantom = g->tune.test_phantom_items;
+  a.mark_neg_inf = g->tune.neg_cycle_mode == BFQ_NEG_CYCLE_MARK ? 1 : 0;
   return a;
 }
 

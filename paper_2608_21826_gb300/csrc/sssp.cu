@@ -86,7 +86,11 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       cur[g] = 0;
       if (act[g]) {
         const long long nd = (long long)label_dist(lab_t[g]) + (long long)cw[g].y;
-        if (nd >= (long long)kInf32) {
+        if (label_dist(lab_t[g]) == kNegInf32) {
+          // minus-infinity tail (only when cycles are resolved): so is the head
+          key[g] = kNegInfLabel;
+          cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
+        } else if (nd >= (long long)kInf32) {
           act[g] = false;
         } else if (nd <= -2147483648LL) {
           raise_status(a.ctl, kStRange);
@@ -108,20 +112,28 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
-          if (nh >= V) {
-            raise_status(a.ctl, kStNegCycle);
-          } else {
-            enq[g] = (r == 2);
-            if (a.cyc && nh >= kCycRecord) {
-              st_relaxed_u64((unsigned long long*)(a.cyc + cw[g].x),
-                             (unsigned long long)pack_edge(tl[g], cw[g].y));
-              if (nh >= walk_at) {
-                if (prove_negative_cycle(a.cyc, a.label, cw[g].x, a.V))
-                  raise_status(a.ctl, kStNegCycle);
-                else
-                  walk_at = nh * 2;
-              }
+          bool proven = nh >= V;          // a walk of >= V edges that still improved
+          if (!proven && a.cyc && nh >= kCycRecord) {
+            st_relaxed_u64((unsigned long long*)(a.cyc + cw[g].x),
+                           (unsigned long long)pack_edge(tl[g], cw[g].y));
+            if (nh >= walk_at) {
+              if (prove_negative_cycle(a.cyc, a.label, cw[g].x, a.V))
+                proven = true;
+              else
+                walk_at = nh * 2;
             }
+          }
+          if (!proven) {
+            enq[g] = (r == 2);
+          } else if (a.mark_neg_inf) {
+            // the head is reached from a negative cycle: minus infinity.  The
+            // second lowering may claim the in-queue flag again if a consumer
+            // took the vertex in between; either claim queues it once more.
+            atomicOr(&a.ctl->status, kStNegCycle);
+            const int r2 = lower_label(&a.label[cw[g].x], kNegInfLabel, key[g] | kQueuedBit);
+            enq[g] = (r == 2) || (r2 == 2);
+          } else {
+            raise_status(a.ctl, kStNegCycle);
           }
         }
       }
@@ -337,7 +349,7 @@ __global__ void sssp_epilogue_kernel(SsspArgs a, int32_t* status_dev, const int*
     const long long l = a.label[v];
     const int d = label_dist(l);
     a.dist[v] = d;
-    if (a.hops) a.hops[v] = (d == kInf32) ? -1 : (int)label_hops(l);
+    if (a.hops) a.hops[v] = (d == kInf32) ? -1 : (d == kNegInf32) ? -2 : (int)label_hops(l);
     if (a.pred) a.pred[v] = -1;
   }
   if (tid == 0) {
@@ -345,6 +357,7 @@ __global__ void sssp_epilogue_kernel(SsspArgs a, int32_t* status_dev, const int*
     int code = BFQ_OK;
     if (bad && *bad) code = BFQ_ERR_INVALID;
     else if (st & (kStTimeout | kStQueue)) code = BFQ_ERR_TIMEOUT;
+    else if (a.mark_neg_inf && (st & kStRange)) code = BFQ_RANGE;   // labels incomplete
     else if (st & kStNegCycle) code = BFQ_NEG_CYCLE;
     else if (st & kStRange) code = BFQ_RANGE;
     a.ctl->last_status = code;
@@ -400,14 +413,18 @@ __global__ void sssp_init_kernel(SsspArgs a) {
 // is valid; following pred strictly lowers hops, so the tree is acyclic.
 __global__ void sssp_pred_kernel(const int* __restrict__ row_ptr, const int2* __restrict__ adj,
                                  const long long* __restrict__ label, int V, int* pred,
-                                 const Control* ctl) {
-  if (ctl && ctl->last_status != 0) return;
+                                 const Control* ctl, int allow_neg_cycle) {
+  // labels are final after a clean run, and after a run that resolved its
+  // negative cycles (minus-infinity vertices match no tight edge below)
+  if (ctl && ctl->last_status != 0 &&
+      !(allow_neg_cycle && ctl->last_status == BFQ_NEG_CYCLE))
+    return;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long u = warp; u < V; u += nw) {
     const long long lu = label_key(label[u]);
-    if (label_dist(lu) == kInf32) continue;
+    if (label_dist(lu) == kInf32 || label_dist(lu) == kNegInf32) continue;
     const int b = row_ptr[u], e = row_ptr[u + 1];
     for (int i = b + lane; i < e; i += 32) {
       const int2 cw = adj[i];
@@ -502,13 +519,13 @@ cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape r
   sssp_epilogue_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a, status_dev, nullptr);
   if (a.pred)
     sssp_pred_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a.row_ptr, a.adj, a.label, a.V,
-                                                                 a.pred, a.ctl);
+                                                                 a.pred, a.ctl, a.mark_neg_inf);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pred_pass(const int* row_ptr, const int2* adj, const long long* label, int V,
                              int* pred, cudaStream_t s) {
-  sssp_pred_kernel<<<1024, 256, 0, s>>>(row_ptr, adj, label, V, pred, nullptr);
+  sssp_pred_kernel<<<1024, 256, 0, s>>>(row_ptr, adj, label, V, pred, nullptr, 0);
   return cudaGetLastError();
 }
 
