@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-rounds", action="store_true")
     p.add_argument("--no-l2", action="store_true")
     p.add_argument("--no-neg-inf", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default run-time parameters (profiling runs)")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
     return p.parse_args()
@@ -149,7 +151,7 @@ def measured_peak_hbm():
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for name in ("sssp.cu", "bfq_device.cuh", "bfq_internal.h"):
+    for name in ("sssp.cu", "sssp_common.cuh", "bfq_device.cuh", "bfq_internal.h"):
         with open(os.path.join(ROOT, "paper_2608_21826_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -549,7 +551,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # run-time parameters picked by the library's autotuner (untimed)
-    tuned = bfq.bfq_autotune(h, srcs)
+    tuned = bfq.bfq_graph_get_tune(h) if args.no_autotune else bfq.bfq_autotune(h, srcs)
     tune_desc = {"share_div": tuned.share_div, "chunk_batch": tuned.chunk_batch,
                  "batch_items": tuned.batch_items}
 

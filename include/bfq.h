@@ -101,7 +101,16 @@ typedef struct bfq_tune {
   int32_t chunk_batch;      /* hub chunks a warp dequeues at once (1..32)    */
   int32_t neg_cycle_mode;   /* BFQ_NEG_CYCLE_STOP or BFQ_NEG_CYCLE_MARK, for
                                bfq_sssp / bfq_sssp_async (see there)         */
-  int32_t reserved[3];
+  int32_t cycle_walk_hops;  /* negative-cycle accelerator: a label of this
+                               many hops makes its lane walk the recorded
+                               relaxation edges behind it looking for a
+                               negative cycle; a failed walk raises that
+                               lane's threshold to twice the label's hops;
+                               edges are recorded from half of it.  2..2^30,
+                               0 = default (64).
+                               Only speed depends on it: hops >= V stays the
+                               exact test.                                   */
+  int32_t reserved[2];
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a

@@ -35,7 +35,8 @@ class Tune(ctypes.Structure):
                 ("spin_limit", ctypes.c_int64), ("time_limit_ms", ctypes.c_int64),
                 ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
-                ("neg_cycle_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):

@@ -38,7 +38,8 @@ struct alignas(16) QueryDesc {
 struct alignas(16) StageHeader {
   int nq;
   int share_div, chunk_batch, batch_items, phantom;
-  int pad[3];
+  int cyc_walk0;                // first cycle-walk threshold (hops)
+  int pad[2];
   long long time_limit_ns, spin_limit;
 };
 
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
   int nbuf = 0;
   WarpCounters wc;
   const MultiEnv env{a.label, a.cyc, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop,
-                     a.qs, hdr.spin_limit};
-  unsigned walk_at = kCycWalkAt;
+                     a.qs, hdr.spin_limit, (unsigned)hdr.cyc_walk0};
+  unsigned walk_at = env.cyc_walk0;     // per lane: hops that trigger a cycle walk
   const unsigned long long t_start = globaltimer_ns();
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
@@ -492,6 +493,11 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
   bfq_batch* b = new (std::nothrow) bfq_batch();
   if (!b) return b_invalid("bfq_batch_create: host allocation failed");
   bfq_tune_default(&b->tune);
+  if (tune && (tune->cycle_walk_hops < 0 || tune->cycle_walk_hops == 1 ||
+               tune->cycle_walk_hops > (1 << 30))) {
+    delete b;
+    return b_invalid("bfq_batch_create: cycle_walk_hops out of range");
+  }
   if (tune) {
     if (tune->share_div) b->tune.share_div = tune->share_div;
     if (tune->chunk_batch) b->tune.chunk_batch = tune->chunk_batch;
@@ -500,6 +506,7 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
     if (tune->time_limit_ms) b->tune.time_limit_ms = tune->time_limit_ms;
     if (tune->queues_per_cta) b->tune.queues_per_cta = tune->queues_per_cta;
     b->tune.test_phantom_items = tune->test_phantom_items;
+    if (tune->cycle_walk_hops) b->tune.cycle_walk_hops = tune->cycle_walk_hops;
   }
   long long maxV = 0, maxC = 0;
   for (int i = 0; i < ngraphs; ++i) {
@@ -638,6 +645,7 @@ int bfq_sssp_batch(bfq_batch_t b, int32_t nq, const int32_t* graph_id, const int
   h->chunk_batch = b->tune.chunk_batch;
   h->batch_items = b->tune.batch_items;
   h->phantom = b->tune.test_phantom_items;
+  h->cyc_walk0 = b->tune.cycle_walk_hops;
   h->time_limit_ns = b->tune.time_limit_ms * 1000000LL;
   h->spin_limit = b->tune.spin_limit;
   cudaStream_t s = (cudaStream_t)stream;
@@ -679,12 +687,14 @@ int bfq_batch_get_stats(bfq_batch_t b, bfq_stats* out) {
 int bfq_batch_set_tune(bfq_batch_t b, const bfq_tune* t) {
   if (!b || !t) return b_invalid("bfq_batch_set_tune: null argument");
   if (t->share_div < 0 || t->chunk_batch < 0 || t->chunk_batch > 32 || t->batch_items < 0 ||
-      t->batch_items > 32)
+      t->batch_items > 32 || t->cycle_walk_hops < 0 || t->cycle_walk_hops == 1 ||
+      t->cycle_walk_hops > (1 << 30))
     return b_invalid("bfq_batch_set_tune: parameter out of range");
   if (t->share_div) b->tune.share_div = t->share_div;
   if (t->chunk_batch) b->tune.chunk_batch = t->chunk_batch;
   if (t->batch_items) b->tune.batch_items = t->batch_items;
   if (t->time_limit_ms) b->tune.time_limit_ms = t->time_limit_ms;
+  if (t->cycle_walk_hops) b->tune.cycle_walk_hops = t->cycle_walk_hops;
   return BFQ_OK;
 }
 

@@ -52,6 +52,7 @@ struct SsspArgs {
   long long time_limit_ns;
   int phantom;                  // test hook: unbacked in-flight items
   int mark_neg_inf;             // 1: resolve negative cycles to minus infinity
+  unsigned cyc_walk0;           // first cycle-walk threshold (hops); records from half
 };
 
 struct LaunchShape {

@@ -135,6 +135,7 @@ int bfq_tune_default(bfq_tune* t) {
   t->l2_persist_pct = 0;
   t->share_div = 2;
   t->chunk_batch = 4;
+  t->cycle_walk_hops = 64;
   return BFQ_OK;
 }
 
@@ -154,6 +155,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (in->share_div) out->share_div = in->share_div;
   if (in->chunk_batch) out->chunk_batch = in->chunk_batch;
   out->neg_cycle_mode = in->neg_cycle_mode;
+  if (in->cycle_walk_hops) out->cycle_walk_hops = in->cycle_walk_hops;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 in this build");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -167,7 +169,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (out->spin_limit < 1 || out->time_limit_ms < 1 || out->ctas_per_sm < 0 ||
       out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0 ||
       out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32 ||
-      (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK))
+      (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK) ||
+      out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30))
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -344,6 +347,7 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.time_limit_ns = g->tune.time_limit_ms * 1000000LL;
   a.phantom = g->tune.test_phantom_items;
   a.mark_neg_inf = g->tune.neg_cycle_mode == BFQ_NEG_CYCLE_MARK ? 1 : 0;
+  a.cyc_walk0 = (unsigned)g->tune.cycle_walk_hops;
   return a;
 }
 

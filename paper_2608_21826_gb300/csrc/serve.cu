@@ -115,6 +115,7 @@ struct ServeArgs {
   int pool_pages;
   int queues_per_cta;
   int share_div, chunk_batch, batch_items;
+  unsigned cyc_walk0;                    // first cycle-walk threshold (hops)
   long long spin_limit, time_limit_ns, idle_exit_ns;
 };
 
@@ -279,8 +280,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
   int nbuf = 0;
   WarpCounters wc;
   const MultiEnv env{a.label, a.cyc, a.inflight, a.qstatus, &a.ctl->status, &a.ctl->stop,
-                     a.qs, a.spin_limit};
-  unsigned walk_at = kCycWalkAt;
+                     a.qs, a.spin_limit, a.cyc_walk0};
+  unsigned walk_at = env.cyc_walk0;     // per lane: hops that trigger a cycle walk
   const unsigned long long t_start = globaltimer_ns();
   unsigned long long t_idle = t_start;
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
@@ -827,6 +828,8 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
     if (tune->batch_items) sv->tune.batch_items = tune->batch_items;
     if (tune->spin_limit) sv->tune.spin_limit = tune->spin_limit;
     if (tune->time_limit_ms) sv->tune.time_limit_ms = tune->time_limit_ms;
+    if (tune->cycle_walk_hops >= 2 && tune->cycle_walk_hops <= (1 << 30))
+      sv->tune.cycle_walk_hops = tune->cycle_walk_hops;
   }
   long long maxC = 0;
   for (int i = 0; i < ngraphs; ++i) {
@@ -876,6 +879,7 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   a.share_div = sv->tune.share_div;
   a.chunk_batch = sv->tune.chunk_batch;
   a.batch_items = sv->tune.batch_items;
+  a.cyc_walk0 = (unsigned)sv->tune.cycle_walk_hops;
   a.spin_limit = sv->tune.spin_limit;
   a.time_limit_ns = sv->tune.time_limit_ms * 1000000LL;
   a.idle_exit_ns = 5LL * 1000000LL;

@@ -113,7 +113,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
           bool proven = nh >= V;          // a walk of >= V edges that still improved
-          if (!proven && a.cyc && nh >= kCycRecord) {
+          if (!proven && a.cyc && nh >= (a.cyc_walk0 >> 1)) {
             st_relaxed_u64((unsigned long long*)(a.cyc + cw[g].x),
                            (unsigned long long)pack_edge(tl[g], cw[g].y));
             if (nh >= walk_at) {
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   unsigned* buf = s_children[wid];
   int nbuf = 0;
-  unsigned walk_at = kCycWalkAt;      // per lane: hops that trigger a cycle walk
+  unsigned walk_at = a.cyc_walk0;     // per lane: hops that trigger a cycle walk
   for (;;) {
     unsigned item = 0;
     int got = 0;

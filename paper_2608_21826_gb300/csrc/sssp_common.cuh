@@ -157,8 +157,10 @@ __device__ __forceinline__ int lower_label(long long* label_v, long long key, lo
 constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per warp step
 
 // Negative-cycle accelerator.  A successful relaxation that gives v a label
-// of kCycRecord hops or more records its edge (tail, weight) in cyc[v], one
-// 8-byte store.  When a label reaches `walk_at` hops the relaxing lane walks
+// of walk0 / 2 hops or more (walk0: the run's first walk threshold) records
+// its edge (tail, weight) in cyc[v], one 8-byte store.  When a label reaches
+// the lane's walk threshold (walk0 at first, twice the label's hops after a
+// failed walk) the lane walks
 // the recorded edges backwards from v (Brent's cycle finding, at most
 // kCycWalk steps).  If they close a cycle, the weights are re-read around it:
 // a closed walk of real edges with negative total weight, through vertices
@@ -166,8 +168,6 @@ constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per wa
 // Nothing else is concluded from the walk, so a racy or stale record can
 // only make a proof fail, never make one up; the hops >= V test remains the
 // exact fallback.
-constexpr unsigned kCycRecord = 128;
-constexpr unsigned kCycWalkAt = 256;
 constexpr int kCycWalk = 32;
 
 __device__ __forceinline__ long long pack_edge(int tail, int w) {

@@ -20,6 +20,7 @@ struct MultiEnv {
   int* gstop;                   // launch-wide stop flag
   QueueSet qs;                  // vertex sub-queues
   long long spin_limit;
+  unsigned cyc_walk0;           // first cycle-walk threshold (hops); records from half
 };
 
 // Count the buffered children in their queries' in-flight counters, then
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
             atomicOr(&e.qstatus[qq[g]], kStNegCycle);
           } else {
             enq[g] = (r == 2);
-            if (e.cyc && nh >= kCycRecord) {
+            if (e.cyc && nh >= (e.cyc_walk0 >> 1)) {
               long long* cb = e.cyc + (lb[g] - e.pool);
               st_relaxed_u64((unsigned long long*)(cb + cw[g].x),
                              (unsigned long long)pack_edge(tl[g], cw[g].y));

@@ -291,3 +291,22 @@ def test_planted_cycle_detected_fast_on_large_graph():
         assert bfq.bfq_get_stats(h)["kernel_ms"] < 200.0
     finally:
         bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("walk", [2, 8, 64, 1 << 30])
+def test_cycle_walk_threshold_changes_speed_only(walk):
+    """Every first-walk threshold gives the same answers: exact labels on a
+    clean deep graph, BFQ_NEG_CYCLE with a planted cycle (at 2^30 only the
+    hops >= V test is left)."""
+    t = bfq.make_tune(cycle_walk_hops=walk)
+    clean = synth.road_graph(128, seed=3)
+    _compare(clean, 0, gpu_util.sssp(clean, 0, tune=t))
+    g = synth.plant_negative_cycle(synth.grid_graph(48, 48, seed=4), 5, seed=6)
+    assert _compare(g, 0, gpu_util.sssp(g, 0, tune=t)) == oracle.NEG_CYCLE
+
+
+def test_cycle_walk_threshold_validated():
+    g = synth.grid_graph(8, 8, seed=1)
+    for bad in (1, -3, (1 << 30) + 1):
+        with pytest.raises(bfq.BfqError):
+            gpu_util.create(g, bfq.make_tune(cycle_walk_hops=bad))
