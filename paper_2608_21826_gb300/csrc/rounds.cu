@@ -195,21 +195,39 @@ __global__ void __launch_bounds__(kRoundsBlock) rounds_kernel(RoundsArgs a) {
             old[g] = ld_relaxed_s64(a.label + cw[g].x);
           }
         }
+        // first compare-and-swap of every group back to back (they overlap)
+        long long prev[kRoundGroups];
+#pragma unroll
+        for (int g = 0; g < kRoundGroups; ++g) {
+          prev[g] = old[g];
+          if (act[g] && key[g] < old[g])
+            prev[g] = (long long)atomicCAS((unsigned long long*)(a.label + cw[g].x),
+                                           (unsigned long long)old[g],
+                                           (unsigned long long)key[g]);
+          else
+            act[g] = false;
+        }
 #pragma unroll
         for (int g = 0; g < kRoundGroups; ++g) {
           if (!act[g]) continue;
-          long long o = old[g];
+          if (prev[g] == old[g]) {
+            ++ch;
+            if (label_hops(key[g]) >= (unsigned)a.V) st |= kStNegCycle;
+            atomicOr(nxt + (cw[g].x >> 5), 1u << (cw[g].x & 31));
+            continue;
+          }
+          long long o = prev[g];
           while (key[g] < o) {
-            const long long prev = (long long)atomicCAS((unsigned long long*)(a.label + cw[g].x),
+            const long long seen = (long long)atomicCAS((unsigned long long*)(a.label + cw[g].x),
                                                         (unsigned long long)o,
                                                         (unsigned long long)key[g]);
-            if (prev == o) {
+            if (seen == o) {
               ++ch;
               if (label_hops(key[g]) >= (unsigned)a.V) st |= kStNegCycle;
               atomicOr(nxt + (cw[g].x >> 5), 1u << (cw[g].x & 31));
               break;
             }
-            o = prev;
+            o = seen;
           }
         }
       }

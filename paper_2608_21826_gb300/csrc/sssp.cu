@@ -101,6 +101,20 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         }
       }
     }
+    // The first compare-and-swap of every group is issued back to back so
+    // the independent atomics overlap; a failed one (another lane changed
+    // the label in between) retries through lower_label.
+    long long prev[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      prev[g] = cur[g];
+      if (act[g] && key[g] < label_key(cur[g]))
+        prev[g] = (long long)atomicCAS((unsigned long long*)&a.label[cw[g].x],
+                                       (unsigned long long)cur[g],
+                                       (unsigned long long)(key[g] | kQueuedBit));
+      else
+        act[g] = false;
+    }
     bool enq[U];
     unsigned item[U];
 #pragma unroll
@@ -108,7 +122,8 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       enq[g] = false;
       item[g] = (unsigned)cw[g].x;
       if (act[g]) {
-        const int r = lower_label(&a.label[cw[g].x], key[g], cur[g]);
+        const int r = (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
+                                          : lower_label(&a.label[cw[g].x], key[g], prev[g]);
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);

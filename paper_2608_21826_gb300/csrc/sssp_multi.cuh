@@ -110,12 +110,26 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
         }
       }
     }
+    // first compare-and-swap of every group back to back (they overlap);
+    // a failed one retries through lower_label
+    long long prev[U];
+#pragma unroll
+    for (int g = 0; g < U; ++g) {
+      prev[g] = cur[g];
+      if (act[g] && key[g] < label_key(cur[g]))
+        prev[g] = (long long)atomicCAS((unsigned long long*)(lb[g] + cw[g].x),
+                                       (unsigned long long)cur[g],
+                                       (unsigned long long)(key[g] | kQueuedBit));
+      else
+        act[g] = false;
+    }
     bool enq[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       enq[g] = false;
       if (act[g]) {
-        const int r = lower_label(lb[g] + cw[g].x, key[g], cur[g]);
+        const int r = (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
+                                          : lower_label(lb[g] + cw[g].x, key[g], prev[g]);
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
