@@ -34,7 +34,7 @@ UNIT = "GTEPS"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "sssp_persistent_rmat22_traffic.txt")
 
 
-def parse():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -55,7 +55,7 @@ def parse():
                    help="keep the default run-time parameters (profiling runs)")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def load_workload(name, rmat_scale=22):
@@ -79,6 +79,21 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def combine_over_ranks(t_seconds, units, device, world_size):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    (MAX) and the work of all ranks (SUM).  There is no data exchange between
+    ranks; this is the only collective, and only for the report."""
+    if world_size <= 1:
+        return float(t_seconds), float(units)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_seconds)], dtype=torch.float64, device=device)
+    mm = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(mm, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(mm.item())
 
 
 class ClockSampler:
@@ -594,15 +609,7 @@ def run_ours(args):
     deq = sum(r[1]["dequeued"] for r in rec)
     k_ms = [r[1]["kernel_ms"] for r in rec]
     n_q = len(rec)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        mm = torch.tensor([m_reached], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(mm, op=dist.ReduceOp.SUM)
-        t_all, m_all = float(tt.item()), float(mm.item())
-    else:
-        t_all, m_all = t_dev, float(m_reached)
+    t_all, m_all = combine_over_ranks(t_dev, m_reached, dev, ws)
     value = m_all / t_all / 1e9
 
     # roofline of the persistent relaxation kernel: algorithmic bytes
@@ -710,7 +717,7 @@ def run_ours(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:
