@@ -262,7 +262,7 @@ def batched_leg(dev, reps=5):
     return out, graphs, handles, queries
 
 
-def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7):
+def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7, tune=None):
     """Poisson arrivals of requests over the batched mix plus an R-MAT scale-23
     graph, at {0.25, 0.5, 0.75, 0.9, 1.1} x the batched saturation q/s;
     latency = submission to completion seen by the server thread.  Baseline:
@@ -280,10 +280,13 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7):
     bufs = [[torch.empty(g.V, dtype=torch.int32, device=dev) for _ in range(ring)] for g in all_g]
     torch.cuda.synchronize()
     budget = 32 * 700_000_000              # label pool of 700M labels (22.4 GB)
-    sv = bfq.bfq_server_create(all_h, budget, 512)
+    # the server runs with the run-time parameters the batch autotuner chose
+    sv = bfq.bfq_server_create(all_h, budget, 512, bfq.make_tune(**tune) if tune else None)
     try:
-        return _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_qps,
-                           n_req)
+        out = _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_qps,
+                          n_req)
+        out["tune"] = tune
+        return out
     finally:
         bfq.bfq_server_destroy(sv)
         bfq.bfq_graph_destroy(h23)
@@ -668,7 +671,7 @@ def run_ours(args):
             if not args.no_serve:
                 try:
                     serve = serve_leg(dev, bgraphs, bhandles, batched["qps"],
-                                      args.serve_requests)
+                                      args.serve_requests, tune=batched["tune"])
                 except Exception as e:                       # reported, not fatal
                     serve = {"error": repr(e)}
         except Exception as e:

@@ -307,7 +307,12 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
  * taking 8 B, 8 B of recorded relaxation edge and 16 B of sub-queue
  * capacity -- has a contiguous run for the
  * graph's V labels; admitted requests join the queries already running on the
- * device.  A host thread drives admission and completion.  tune may be NULL. */
+ * device.  One exception to arrival order: a request whose labels exceed a
+ * quarter of the device's L2 (V >= L2 bytes / 32; such a query keeps the GPU
+ * busy alone, and two of them evict each other's labels) runs only while no
+ * other such request runs, and smaller requests behind it may be admitted
+ * while it waits.  A host thread drives admission and completion.  tune may
+ * be NULL. */
 int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
                       int64_t hbm_budget_bytes, int32_t max_slots, const bfq_tune* tune);
 /* Queue a request (thread-safe).  dist / hops: caller-owned device arrays of

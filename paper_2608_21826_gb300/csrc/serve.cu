@@ -48,6 +48,7 @@ namespace {
 
 constexpr int kPageLog2 = 12;            // label pool page: 4096 labels
 constexpr int kTaskLog2 = 14;            // init / unpack task: 16384 labels
+constexpr int kMaxHelpers = 128;         // helper items queued per init / unpack phase
 constexpr int kChunkIdBits = 20;         // chunk item = slot << 20 | chunk
 constexpr int kMaxSlots = 2048;          // 11 bits of slot in task items
 
@@ -95,7 +96,21 @@ struct alignas(128) ServeCtl {
   int bad_where;                         // first failed range check (0 = none)
   unsigned bad_value;
   int pad6[30];
+  unsigned long long poll_ns;            // last look at the host rings (0: look now)
+  unsigned long long pad7[15];
 };
+
+// Reads of the mapped host rings cross the chip-to-host link; at most one
+// warp looks at a time, and not more often than this.
+constexpr unsigned long long kHostPollGapNs = 2000;
+
+// Claim the next look at the host memory: true for one warp per gap.
+__device__ __forceinline__ bool claim_host_poll(ServeCtl* ctl) {
+  const unsigned long long now = globaltimer_ns();
+  const unsigned long long last = ld_relaxed_u64(&ctl->poll_ns);
+  if (last != 0 && now - last < kHostPollGapNs) return false;
+  return atomicCAS(&ctl->poll_ns, last, now) == last;
+}
 
 struct ServeArgs {
   SlotDesc* slots;                       // [S]
@@ -152,7 +167,7 @@ __device__ __noinline__ void serve_bad(const ServeArgs& a, int where, unsigned v
   st_relaxed_s32(&a.ctl->stop, 1);
 }
 
-// Publish `n` task items (kind, slot, 0..n-1) to the task queue.
+// Publish `n` helper items (kind, slot, 0..n-1) to the task queue.
 __device__ __forceinline__ bool push_tasks(const ServeArgs& a, int kind, int slot, int n,
                                            int lane) {
   for (int base = 0; base < n; base += 32) {
@@ -168,20 +183,22 @@ __device__ __forceinline__ bool push_tasks(const ServeArgs& a, int kind, int slo
 // Take the next admission command, if one is ready, into its slot.
 __device__ __forceinline__ bool admit_one(const ServeArgs& a, int lane) {
   int slot = -1, n_tasks = 0;
-  if (lane == 0) {
+  if (lane == 0 && claim_host_poll(a.ctl)) {
     const unsigned pos = ld_relaxed_s32((const int*)&a.ctl->cmd_head);
     ServeCmd* c = a.cmd + (pos % (unsigned)a.ring);
     if (ld_acquire_sys_u32(&c->seq) == pos + 1 &&
         atomicCAS(&a.ctl->cmd_head, pos, pos + 1) == pos) {
+      st_relaxed_u64(&a.ctl->poll_ns, 0ull);   // commands come in bursts: look again now
       slot = c->slot;
       SlotDesc d = c->d;
       d.n_tasks = (d.V + (1 << kTaskLog2) - 1) >> kTaskLog2;
       a.slots[slot] = d;
       a.qstatus[slot] = 0;
       a.inflight[slot * kCounterStride] = 0;
-      a.pending[slot * kCounterStride] = d.n_tasks;
+      n_tasks = min(d.n_tasks, kMaxHelpers);        // helper items
+      a.pending[slot * kCounterStride] = n_tasks;
+      a.pending[slot * kCounterStride + 1] = 0;     // task cursor
       atomicAdd(&a.ctl->active, 1);
-      n_tasks = d.n_tasks;
       __threadfence();               // slot state before its tasks are visible
     }
   }
@@ -193,44 +210,68 @@ __device__ __forceinline__ bool admit_one(const ServeArgs& a, int lane) {
   return true;
 }
 
-// Init task: labels of [t * 16384, ...) of the slot to infinity (the source
-// to (0, 0), queued), page owners; the last one queues the source.
-// Unpack task: dist / hops out; the last one posts the completion.
+// Init and unpack phases of a slot: the slot's V labels are cut into tasks
+// of 16384; the phase queues min(tasks, kMaxHelpers) helper items, and a warp
+// holding one claims tasks from the slot's cursor (pending[slot * stride + 1],
+// an atomicAdd, no retries) until none is left, so a large graph needs few
+// queue operations.  The phase ends when every helper has left (helpers'
+// count in pending[slot * stride]); no helper of it is running afterwards,
+// so the slot's next phase may reset the cursor.
+// Init task: labels of [t * 16384, ...) to infinity (the source to (0, 0),
+// queued), page owners; the last helper queues the source.
+// Unpack task: dist / hops out; the last helper posts the completion.
 __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int lane, int home) {
   const int kind = (int)(id >> 30);
   const int slot = (int)((id >> 19) & (kMaxSlots - 1));
-  const int t = (int)(id & ((1u << 19) - 1));
+  const int h = (int)(id & ((1u << 19) - 1));
   if (slot >= a.max_slots) {
     if (lane == 0) serve_bad(a, 1, id);
     return false;
   }
   const SlotDesc d = a.slots[slot];
-  if (t >= d.n_tasks || d.label_off < 0 ||
+  if (h >= kMaxHelpers || d.label_off < 0 ||
       ((long long)d.label_off + d.V) > ((long long)a.pool_pages << kPageLog2)) {
     if (lane == 0) serve_bad(a, 2, id);
     return false;
   }
-  const int lo = t << kTaskLog2;
-  const int hi = min(d.V, lo + (1 << kTaskLog2));
   long long* lab = a.label + d.label_off;
-  if (kind == 0) {
-    for (int i = lo + lane; i < hi; i += 32)
-      lab[i] = (i == d.src) ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
-    const int p0 = (d.label_off + lo) >> kPageLog2, p1 = (d.label_off + hi - 1) >> kPageLog2;
-    for (int p = p0 + lane; p <= p1; p += 32) a.page_owner[p] = slot;
-  } else if (d.dist || d.hops) {
-    // eight labels in flight per lane
-    for (int i0 = lo + lane; i0 < hi; i0 += 32 * 8) {
-      long long l[8];
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&a.pending[slot * kCounterStride + 1], 1);
+    t = __shfl_sync(kFullMask, t, 0);
+    if (t >= d.n_tasks) break;
+    const int lo = t << kTaskLog2;
+    const int hi = min(d.V, lo + (1 << kTaskLog2));
+    if (kind == 0) {
+      for (int i = lo + lane; i < hi; i += 32)
+        lab[i] = (i == d.src) ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
+      const int p0 = (d.label_off + lo) >> kPageLog2, p1 = (d.label_off + hi - 1) >> kPageLog2;
+      for (int p = p0 + lane; p <= p1; p += 32) a.page_owner[p] = slot;
+    } else if (d.dist || d.hops) {
+      // sixteen labels in flight per lane, read as 16-byte pairs (the slot's
+      // labels start on a page, so even indices are 16-byte aligned)
+      for (int i0 = lo + 2 * lane; i0 < hi; i0 += 64 * 8) {
+        long long l[16];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) l[k] = (i0 + 32 * k < hi) ? lab[i0 + 32 * k] : 0;
+        for (int k = 0; k < 8; ++k) {
+          const int i = i0 + 64 * k;
+          if (i + 1 < hi) {
+            const longlong2 v = *reinterpret_cast<const longlong2*>(lab + i);
+            l[2 * k] = v.x;
+            l[2 * k + 1] = v.y;
+          } else {
+            l[2 * k] = (i < hi) ? lab[i] : 0;
+            l[2 * k + 1] = 0;
+          }
+        }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = i0 + 32 * k;
-        if (i >= hi) break;
-        const int dd = label_dist(l[k]);
-        if (d.dist) d.dist[i] = dd;
-        if (d.hops) d.hops[i] = (dd == kInf32) ? -1 : (int)label_hops(l[k]);
+        for (int k = 0; k < 16; ++k) {
+          const int i = i0 + 64 * (k >> 1) + (k & 1);
+          if (i >= hi) continue;
+          const int dd = label_dist(l[k]);
+          if (d.dist) d.dist[i] = dd;
+          if (d.hops) d.hops[i] = (dd == kInf32) ? -1 : (int)label_hops(l[k]);
+        }
       }
     }
   }
@@ -296,10 +337,11 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
       since_admit = 0;
       if (admit_one(a, lane)) idle = 0;
     }
-    // 1) init / unpack tasks
+    // 1) init / unpack tasks (the one task sub-queue is looked at every
+    // eighth step of a busy warp: its counter line is shared by all warps)
     unsigned item = 0;
     int c = 0;
-    if (lane == 0) c = ld_relaxed_s32(&a.tq.meta[0].count);
+    if (lane == 0) c = ((since_admit & 7) == 0 || idle) ? ld_relaxed_s32(&a.tq.meta[0].count) : 0;
     else if (lane == 1) c = ld_relaxed_s32(&a.cq.meta[chome].count);
     else if (lane == 2) c = ld_relaxed_s32(&a.qs.meta[home].count);
     const int c_task = __shfl_sync(kFullMask, c, 0);
@@ -359,7 +401,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
         const unsigned long long now = globaltimer_ns();
         if (ld_relaxed_s32(&a.ctl->stop)) {
           leave = 1;
-        } else if (ld_acquire_sys_s32(a.shutdown) ||
+        } else if ((claim_host_poll(a.ctl) && ld_acquire_sys_s32(a.shutdown)) ||
                    (long long)(now - t_start) > a.time_limit_ns ||
                    (ld_relaxed_s32(&a.ctl->active) == 0 &&
                     (long long)(now - t_idle) > a.idle_exit_ns)) {
@@ -497,8 +539,9 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
       const int s = __shfl_sync(kFullMask, emptied, src_lane);
       int n_tasks = 0;
       if (lane == 0) {
-        n_tasks = a.slots[s].n_tasks;
+        n_tasks = min(a.slots[s].n_tasks, kMaxHelpers);   // helper items
         a.pending[s * kCounterStride] = n_tasks;
+        a.pending[s * kCounterStride + 1] = 0;              // task cursor
         __threadfence();
       }
       __syncwarp();
@@ -539,6 +582,7 @@ __global__ void serve_reset_kernel(ServeArgs a) {
     a.ctl->active = 0;
     a.ctl->stop = 0;
     a.ctl->status = 0;
+    a.ctl->poll_ns = 0;
   }
 }
 
@@ -589,7 +633,17 @@ struct bfq_server {
   std::condition_variable cv;
   std::deque<ServeRequest> pending;
   std::unordered_map<int64_t, ServeRecord> records;
-  std::unordered_map<int64_t, std::pair<int, std::pair<long long, long long>>> admitted;  // id -> slot, page run
+  struct Admitted {
+    int slot;
+    long long start, pages;    // page run of its labels
+    bool large;
+  };
+  std::unordered_map<int64_t, Admitted> admitted;
+  // Requests whose labels exceed a quarter of L2 keep a GPU busy alone and,
+  // run side by side, push each other's labels out of L2: at most one runs
+  // at a time, and smaller requests may pass one that waits for its turn.
+  long long large_vertices = 0;
+  int large_active = 0;
   std::vector<int> free_slots;
   std::map<long long, long long> free_pages;        // start page -> page count
   int64_t next_id = 1;
@@ -645,6 +699,7 @@ struct bfq_server {
       }
     }
     admitted.clear();
+    large_active = 0;
     for (auto& rq : pending) {
       auto rec = records.find(rq.id);
       if (rec != records.end()) {
@@ -700,8 +755,9 @@ struct bfq_server {
         progressed = true;
         auto ad = admitted.find(id);
         if (ad != admitted.end()) {
-          free_slots.push_back(ad->second.first);
-          free_run(ad->second.second.first, ad->second.second.second);
+          free_slots.push_back(ad->second.slot);
+          free_run(ad->second.start, ad->second.pages);
+          if (ad->second.large) --large_active;
           admitted.erase(ad);
         }
         auto rec = records.find(id);
@@ -711,10 +767,17 @@ struct bfq_server {
         }
         ++completed;
       }
-      // admissions, FIFO: the head waits until it fits
-      while (!pending.empty() && !free_slots.empty() && !fatal) {
-        ServeRequest& rq = pending.front();
+      // admissions in FIFO order: a request waits until it fits, and those
+      // behind it wait too, except behind a large request that waits for the
+      // large one running now
+      for (size_t i = 0; i < pending.size() && i < 1024 && !free_slots.empty() && !fatal;) {
+        ServeRequest& rq = pending[i];
         const GraphView& gv = views[rq.graph];
+        const bool large = gv.V >= large_vertices;
+        if (large && large_active > 0) {
+          ++i;
+          continue;
+        }
         const long long need = ((long long)gv.V + (1 << kPageLog2) - 1) >> kPageLog2;
         long long start = 0;
         if (!alloc_pages(need, &start)) break;
@@ -739,8 +802,9 @@ struct bfq_server {
         c->slot = slot;
         __atomic_store_n(&c->seq, cmd_tail + 1, __ATOMIC_RELEASE);
         ++cmd_tail;
-        admitted[rq.id] = {slot, {start, need}};
-        pending.pop_front();
+        admitted[rq.id] = Admitted{slot, start, need, large};
+        if (large) ++large_active;
+        pending.erase(pending.begin() + (long)i);
         progressed = true;
         peak_active = std::max<long long>(peak_active, (long long)admitted.size());
       }
@@ -775,10 +839,11 @@ struct bfq_server {
               rec->second.status = BFQ_ERR_TIMEOUT;
               rec->second.t_done = now_ns();
             }
-            free_slots.push_back(kv.second.first);
-            free_run(kv.second.second.first, kv.second.second.second);
+            free_slots.push_back(kv.second.slot);
+            free_run(kv.second.start, kv.second.pages);
           }
           admitted.clear();
+          large_active = 0;
           serve_reset_kernel<<<1024, 256, 0, stream>>>(args);
           cudaMemcpyAsync(&args.ctl->cmd_head, &cmd_tail, sizeof(unsigned), cudaMemcpyHostToDevice,
                           stream);
@@ -858,6 +923,9 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
       per_sm < 1)
     per_sm = 1;
   sv->grid = sms * per_sm;
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  sv->large_vertices = std::max<long long>(1LL << 20, (long long)l2 / 4 / (long long)sizeof(long long));
   ServeArgs& a = sv->args;
   a.queues_per_cta = 1;
   a.qs.Q = sv->grid;
@@ -872,7 +940,8 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   long long max_tasks = 1;
   for (const GraphView& gv : sv->views)
     max_tasks = std::max<long long>(max_tasks, (gv.V + (1LL << kTaskLog2) - 1) >> kTaskLog2);
-  a.tq.cap_log2 = std::max(10, ceil_log2_s((long long)max_slots * max_tasks));
+  a.tq.cap_log2 = std::max(10, ceil_log2_s((long long)max_slots *
+                                           std::min<long long>(max_tasks, kMaxHelpers)));
   a.ring = sv->ring;
   a.max_slots = max_slots;
   a.pool_pages = (int)(entries >> kPageLog2);
