@@ -110,7 +110,14 @@ typedef struct bfq_tune {
                                0 = default (64).
                                Only speed depends on it: hops >= V stays the
                                exact test.                                   */
-  int32_t reserved[2];
+  int32_t relax_atomic;     /* how bfq_sssp lowers a label: BFQ_RELAX_AUTO,
+                               BFQ_RELAX_MIN (one atomicMin per edge: fastest
+                               while the label array sits in L2, but every
+                               atomic dirties its line) or BFQ_RELAX_CAS (load,
+                               then compare-and-swap only when lower).  AUTO
+                               takes MIN when 8 V <= half of L2.  Results are
+                               the same either way.                          */
+  int32_t reserved[1];
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
@@ -126,6 +133,11 @@ typedef struct bfq_tune {
  * round-based and allocation-free entry points always STOP. */
 #define BFQ_NEG_CYCLE_STOP 0
 #define BFQ_NEG_CYCLE_MARK 1
+
+/* bfq_tune.relax_atomic */
+#define BFQ_RELAX_AUTO 0
+#define BFQ_RELAX_MIN 1
+#define BFQ_RELAX_CAS 2
 
 /* Counters of the last finished run on a graph handle (summed over warps). */
 typedef struct bfq_stats {

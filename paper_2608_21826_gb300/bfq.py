@@ -36,7 +36,7 @@ class Tune(ctypes.Structure):
                 ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
                 ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("relax_atomic", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -59,6 +59,7 @@ class RoundsStats(ctypes.Structure):
 
 ROUNDS_ALL_EDGES = 1
 NEG_CYCLE_STOP, NEG_CYCLE_MARK = 0, 1
+RELAX_AUTO, RELAX_MIN, RELAX_CAS = 0, 1, 2
 NEG_INF = -2147483648          # dist of a vertex reachable from a negative cycle (MARK)
 
 _VP = ctypes.c_void_p

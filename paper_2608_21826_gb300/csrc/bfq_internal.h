@@ -53,6 +53,7 @@ struct SsspArgs {
   int phantom;                  // test hook: unbacked in-flight items
   int mark_neg_inf;             // 1: resolve negative cycles to minus infinity
   unsigned cyc_walk0;           // first cycle-walk threshold (hops); records from half
+  int relax_min;                // 1: relax with one atomicMin (labels fit in L2)
 };
 
 struct LaunchShape {

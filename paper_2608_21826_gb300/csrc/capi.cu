@@ -62,6 +62,7 @@ struct bfq_graph {
   long long bytes = 0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the persistent kernel
+  long long l2_bytes = 0;                      // device L2 size
   int l2_pct_applied = 0;                      // l2_persist_pct the window was made for
   size_t l2_limit_saved = 0;                   // persisting-L2 limit before the first window
   cudaAccessPolicyWindow l2win{};
@@ -156,6 +157,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (in->chunk_batch) out->chunk_batch = in->chunk_batch;
   out->neg_cycle_mode = in->neg_cycle_mode;
   if (in->cycle_walk_hops) out->cycle_walk_hops = in->cycle_walk_hops;
+  out->relax_atomic = in->relax_atomic;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 in this build");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -170,7 +172,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       out->l2_persist_pct < 0 || out->l2_persist_pct > 100 || out->test_phantom_items < 0 ||
       out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32 ||
       (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK) ||
-      out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30))
+      out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30) ||
+      out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_CAS)
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -268,6 +271,9 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   // launch shape
   int sms = 0;
   G_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+  int l2 = 0;
+  G_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device));
+  g->l2_bytes = l2;
   const int block = g->tune.threads_per_cta;
   int per_sm = sssp_max_ctas_per_sm(block);
   if (g->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, g->tune.ctas_per_sm);
@@ -348,6 +354,10 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.phantom = g->tune.test_phantom_items;
   a.mark_neg_inf = g->tune.neg_cycle_mode == BFQ_NEG_CYCLE_MARK ? 1 : 0;
   a.cyc_walk0 = (unsigned)g->tune.cycle_walk_hops;
+  // one atomicMin per relaxation while the label array fits in half of L2
+  a.relax_min = g->tune.relax_atomic == BFQ_RELAX_MIN ? 1
+                : g->tune.relax_atomic == BFQ_RELAX_CAS ? 0
+                : (long long)sizeof(long long) * g->V <= g->l2_bytes / 2 ? 1 : 0;
   return a;
 }
 

@@ -189,6 +189,7 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   a.spin_limit = 1LL << 22;
   a.time_limit_ns = 20000LL * 1000000LL;
   a.phantom = 0;
+  a.relax_min = 1;                 // at most 4 MiB of labels: they stay in L2
   int* bad = (int*)(base + L.bad);
 
   BFQ_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));

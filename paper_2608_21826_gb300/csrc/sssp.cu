@@ -46,7 +46,7 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 // the groups overlap.  Returns false on a timeout.
 // Claimed children are appended to the warp's buffer `buf` (nbuf items,
 // capacity kChildBuf) and published in bulk by flush_children.
-template <int U>
+template <int U, bool MIN>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
                                              long long lab, int tail, int lane, int home,
                                              WarpCounters& wc, unsigned* buf, int& nbuf,
@@ -89,7 +89,6 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         if (label_dist(lab_t[g]) == kNegInf32) {
           // minus-infinity tail (only when cycles are resolved): so is the head
           key[g] = kNegInfLabel;
-          cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
         } else if (nd >= (long long)kInf32) {
           act[g] = false;
         } else if (nd <= -2147483648LL) {
@@ -97,23 +96,36 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
           act[g] = false;
         } else {
           key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
-          cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
         }
+        if (act[g] && !MIN) cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
       }
     }
-    // The first compare-and-swap of every group is issued back to back so
-    // the independent atomics overlap; a failed one (another lane changed
-    // the label in between) retries through lower_label.
     long long prev[U];
+    if (MIN) {
+      // One atomicMin per edge lowers the label and claims the in-queue flag
+      // at once: keys are even (bit 0 is the flag), so key | 1 is below a
+      // label exactly when key is below the label's key part, and the
+      // minimum then carries the flag.  Used while the label array sits in
+      // L2: every atomic, lowering or not, dirties its line.
 #pragma unroll
-    for (int g = 0; g < U; ++g) {
-      prev[g] = cur[g];
-      if (act[g] && key[g] < label_key(cur[g]))
-        prev[g] = (long long)atomicCAS((unsigned long long*)&a.label[cw[g].x],
-                                       (unsigned long long)cur[g],
-                                       (unsigned long long)(key[g] | kQueuedBit));
-      else
-        act[g] = false;
+      for (int g = 0; g < U; ++g) {
+        prev[g] = 0;
+        if (act[g]) cur[g] = atomicMin(&a.label[cw[g].x], key[g] | kQueuedBit);
+      }
+    } else {
+      // Load, then the first compare-and-swap of every group back to back
+      // (the independent atomics overlap); a failed one (another lane
+      // changed the label in between) retries through lower_label.
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        prev[g] = cur[g];
+        if (act[g] && key[g] < label_key(cur[g]))
+          prev[g] = (long long)atomicCAS((unsigned long long*)&a.label[cw[g].x],
+                                         (unsigned long long)cur[g],
+                                         (unsigned long long)(key[g] | kQueuedBit));
+        else
+          act[g] = false;
+      }
     }
     bool enq[U];
     unsigned item[U];
@@ -122,8 +134,10 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       enq[g] = false;
       item[g] = (unsigned)cw[g].x;
       if (act[g]) {
-        const int r = (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
-                                          : lower_label(&a.label[cw[g].x], key[g], prev[g]);
+        const int r =
+            MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
+                        : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
+                                              : lower_label(&a.label[cw[g].x], key[g], prev[g]);
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
@@ -170,6 +184,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
 
 // Publish the hub chunks [c0_j, c0_j + nch_j) of the lanes with nch > 0 to
 // the chunk sub-queues.  Chunks that find no room are relaxed right here.
+template <bool MIN>
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
                                             int home, int chome, WarpCounters& wc,
                                             unsigned* buf, int& nbuf, unsigned& walk_at) {
@@ -204,7 +219,7 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
         tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged<kGroups>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
                                  walk_at) ||
           !flush_children(a, home, buf, nbuf, lane, wc))
         return false;
@@ -214,6 +229,9 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
   return true;
 }
 
+// MIN: lower labels with one atomicMin per edge (see relax_merged); both
+// forms are compiled and the launcher picks one per run.
+template <bool MIN>
 __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_kernel(SsspArgs a) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -317,12 +335,12 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at)) {
+      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at)) {
         timed_out = true;
         break;
       }
     }
-    if (!relax_merged<kGroups>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
                                walk_at) ||
         !flush_children(a, home, buf, nbuf, lane, wc)) {
       timed_out = true;
@@ -504,7 +522,7 @@ __global__ void queue_reset_kernel(QueueSet qs) {
 
 int sssp_max_ctas_per_sm(int block) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_persistent_kernel, block, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_persistent_kernel<true>, block, 0) !=
       cudaSuccess)
     return 1;
   return n < 1 ? 1 : n;
@@ -525,10 +543,14 @@ cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape r
     attr[0].val.accessPolicyWindow = *l2win;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, sssp_persistent_kernel, a);
+    const cudaError_t e = a.relax_min ? cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<true>, a)
+                                      : cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<false>, a);
     if (e != cudaSuccess) return e;
   } else {
-    sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+    if (a.relax_min)
+      sssp_persistent_kernel<true><<<run_shape.grid, run_shape.block, 0, s>>>(a);
+    else
+      sssp_persistent_kernel<false><<<run_shape.grid, run_shape.block, 0, s>>>(a);
   }
   if (ev1) cudaEventRecord(ev1, s);
   sssp_epilogue_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a, status_dev, nullptr);
@@ -571,7 +593,10 @@ cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s) {
 
 cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
                                         cudaStream_t s) {
-  sssp_persistent_kernel<<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  if (a.relax_min)
+    sssp_persistent_kernel<true><<<run_shape.grid, run_shape.block, 0, s>>>(a);
+  else
+    sssp_persistent_kernel<false><<<run_shape.grid, run_shape.block, 0, s>>>(a);
   return cudaGetLastError();
 }
 

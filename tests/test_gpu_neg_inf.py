@@ -80,6 +80,15 @@ def test_random_with_cycles(seed):
     _compare(g, src, _one(g, src), check_pred=True)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_random_with_cycles_cas_relaxation(seed):
+    rng = np.random.default_rng(50 + seed)
+    V = int(rng.integers(100, 3000))
+    g = synth.random_graph(V, 5 * V, seed=900 + seed, wlo=-3, whi=40)
+    t = bfq.make_tune(neg_cycle_mode=bfq.NEG_CYCLE_MARK, relax_atomic=bfq.RELAX_CAS)
+    _compare(g, 0, gpu_util.sssp(g, 0, tune=t, want_pred=True), check_pred=True)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_planted_cycles_grid(seed):
     base = synth.grid_graph(64, 64, seed=seed)

@@ -125,6 +125,9 @@ def test_rmat22_full_all_sources():
     dict(queues_per_cta=4),
     dict(ctas_per_sm=1),
     dict(hub_degree=64, chunk_edges=32, batch_items=4, queues_per_cta=2),
+    dict(relax_atomic=1),
+    dict(relax_atomic=2),
+    dict(relax_atomic=2, hub_degree=32, chunk_edges=32, batch_items=4),
 ], ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
 def test_tunes(tune):
     g = synth.workload_rmat(14)
@@ -293,12 +296,13 @@ def test_planted_cycle_detected_fast_on_large_graph():
         bfq.bfq_graph_destroy(h)
 
 
+@pytest.mark.parametrize("relax", [1, 2])
 @pytest.mark.parametrize("walk", [2, 8, 64, 1 << 30])
-def test_cycle_walk_threshold_changes_speed_only(walk):
+def test_cycle_walk_threshold_changes_speed_only(walk, relax):
     """Every first-walk threshold gives the same answers: exact labels on a
     clean deep graph, BFQ_NEG_CYCLE with a planted cycle (at 2^30 only the
     hops >= V test is left)."""
-    t = bfq.make_tune(cycle_walk_hops=walk)
+    t = bfq.make_tune(cycle_walk_hops=walk, relax_atomic=relax)
     clean = synth.road_graph(128, seed=3)
     _compare(clean, 0, gpu_util.sssp(clean, 0, tune=t))
     g = synth.plant_negative_cycle(synth.grid_graph(48, 48, seed=4), 5, seed=6)
