@@ -205,7 +205,7 @@ def cpu_baseline(g, n_sources=1):
                       f"{t_total:.1f} s on 1 core of {os.cpu_count()}"}
 
 
-def batched_leg(dev, reps=5):
+def batched_leg(dev, reps=5, autotune=True):
     """The batched mix: 64 graphs (V log-uniform in [1e3,1e6], degree U[4,16],
     grid / R-MAT alternating, 6 with a planted negative cycle), 8 sources each
     = 512 queries in one launch (captured CUDA graph, autotuned), against the
@@ -218,7 +218,11 @@ def batched_leg(dev, reps=5):
     total = int(sum(graphs[g].V for g, _ in queries))
     b = bfq.bfq_batch_create(handles, nq, total)
     dist = [torch.empty(graphs[g].V, dtype=torch.int32, device=dev) for g, _ in queries]
-    tune = bfq.bfq_batch_autotune(b, queries[:, 0], queries[:, 1], dist)
+    if autotune:
+        tune = bfq.bfq_batch_autotune(b, queries[:, 0], queries[:, 1], dist)
+    else:                                   # profiling runs: the usual choice
+        tune = bfq.make_tune(share_div=1, chunk_batch=8, batch_items=32)
+        bfq.bfq_batch_set_tune(b, tune)
     for _ in range(2):
         bfq.bfq_sssp_batch(b, queries[:, 0], queries[:, 1], dist)
     ms = []
@@ -667,7 +671,7 @@ def run_ours(args):
     if not args.no_batched:
         bhandles = []
         try:
-            batched, bgraphs, bhandles, _ = batched_leg(dev)
+            batched, bgraphs, bhandles, _ = batched_leg(dev, autotune=not args.no_autotune)
             if not args.no_serve:
                 try:
                     serve = serve_leg(dev, bgraphs, bhandles, batched["qps"],

@@ -117,7 +117,13 @@ typedef struct bfq_tune {
                                then compare-and-swap only when lower).  AUTO
                                takes MIN when 8 V <= half of L2.  Results are
                                the same either way.                          */
-  int32_t reserved[1];
+  int32_t batch_budget_klabels; /* batched queries: labels (in units of 1024)
+                               of the queries running at once.  Queries start
+                               in order while the running ones fit, so their
+                               labels stay in L2; one always runs.  The server
+                               admits requests below its large-request size
+                               by the same budget.  0 = half of L2 (8-byte
+                               labels); -1 = no budget                      */
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
@@ -323,8 +329,10 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
  * quarter of the device's L2 (V >= L2 bytes / 32; such a query keeps the GPU
  * busy alone, and two of them evict each other's labels) runs only while no
  * other such request runs, and smaller requests behind it may be admitted
- * while it waits.  A host thread drives admission and completion.  tune may
- * be NULL. */
+ * while it waits.  The other requests are admitted while their labels fit
+ * tune->batch_budget_klabels (default: half of L2), so the labels being
+ * relaxed stay in L2; one always runs.  A host thread drives admission and
+ * completion.  tune may be NULL. */
 int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
                       int64_t hbm_budget_bytes, int32_t max_slots, const bfq_tune* tune);
 /* Queue a request (thread-safe).  dist / hops: caller-owned device arrays of

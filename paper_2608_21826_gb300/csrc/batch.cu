@@ -39,8 +39,11 @@ struct alignas(16) StageHeader {
   int nq;
   int share_div, chunk_batch, batch_items, phantom;
   int cyc_walk0;                // first cycle-walk threshold (hops)
-  int pad[2];
+  int window;                   // queries started by the init kernel
+  int pad;
   long long time_limit_ns, spin_limit;
+  long long budget;             // labels of the queries running at once (soft)
+  long long pad1;
 };
 
 struct alignas(128) BatchCtl {
@@ -54,6 +57,12 @@ struct alignas(128) BatchCtl {
   unsigned long long pad3[8];
   int last_status;              // 0, or an error code that needs a queue reset
   int pad4[31];
+  int next_q;                   // next query to start
+  int pad5[31];
+  int active;                   // queries started and not finished
+  int pad6[31];
+  long long active_labels;      // their labels
+  long long pad7[15];
 };
 
 struct BatchArgs {
@@ -86,6 +95,42 @@ __device__ __forceinline__ int find_query(const int* off, int nq, int x) {
 __device__ __forceinline__ void batch_timeout(const BatchArgs& a) {
   atomicOr(&a.ctl->status, kStTimeout);
   st_relaxed_s32(&a.ctl->stop, 1);
+}
+
+// Queries start in order while the labels of the running ones stay within
+// the budget (half of L2 by default): the labels of a few dozen running
+// queries then stay in L2 instead of all of them being touched at random
+// in HBM.  A query that finishes frees its share and starts the next ones;
+// one always runs.  Returns false if a source could not be queued.
+__device__ __forceinline__ bool start_queries(const BatchArgs& a, const StageHeader& hdr,
+                                              const int* s_loff, int lane, int home) {
+  for (;;) {
+    int q = -1;
+    if (lane == 0) {
+      const int n = ld_relaxed_s32(&a.ctl->next_q);
+      if (n < hdr.nq) {
+        const long long v = (long long)s_loff[n + 1] - s_loff[n];
+        if (ld_relaxed_s32(&a.ctl->active) == 0 ||
+            (long long)ld_relaxed_u64((unsigned long long*)&a.ctl->active_labels) + v <= hdr.budget) {
+          if (atomicCAS(&a.ctl->next_q, n, n + 1) == n) {
+            atomicAdd((unsigned long long*)&a.ctl->active_labels, (unsigned long long)v);
+            atomicAdd(&a.ctl->active, 1);
+            a.inflight[n * kCounterStride] = 1 + hdr.phantom;
+            q = n;
+          } else {
+            q = -2;                                // lost the race: look again
+          }
+        }
+      }
+    }
+    q = __shfl_sync(kFullMask, q, 0);
+    if (q == -2) continue;
+    if (q < 0) return true;
+    __syncwarp();                                  // in-flight count before the source
+    const unsigned item = (unsigned)(s_loff[q] + a.desc[q].src);
+    if (enqueue_warp(a.qs, home, lane == 0, item, lane, hdr.spin_limit, 4LL * a.qs.Q + 64) != 1)
+      return false;
+  }
 }
 
 __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_kernel(BatchArgs a) {
@@ -276,7 +321,17 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       break;
     }
     __syncwarp();
-    if (retire_multi(env, lane < got ? q : -1, lane) >= 0) atomicAdd(&a.ctl->remaining, -1);
+    const int emptied = retire_multi(env, lane < got ? q : -1, lane);
+    if (emptied >= 0) {
+      atomicAdd(&a.ctl->remaining, -1);
+      atomicAdd((unsigned long long*)&a.ctl->active_labels,
+                (unsigned long long)(-((long long)s_loff[emptied + 1] - s_loff[emptied])));
+      atomicAdd(&a.ctl->active, -1);
+    }
+    if (__any_sync(kFullMask, emptied >= 0) && !start_queries(a, hdr, s_loff, lane, home)) {
+      timed_out = true;
+      break;
+    }
     int stop = 0;
     if (lane == 0) stop = ld_relaxed_s32(&a.ctl->stop);
     if (__shfl_sync(kFullMask, stop, 0)) break;
@@ -327,7 +382,13 @@ __global__ void batch_init_kernel(BatchArgs a) {
     const bool is_src = (i - s_off[q]) == a.desc[q].src;
     a.label[i] = is_src ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
   }
+  const int window = a.hdr->window;
   for (long long q = tid; q < nq; q += nth) {
+    a.qstatus[q] = 0;
+    if (q >= window) {                       // started later by start_queries
+      a.inflight[q * kCounterStride] = 0;
+      continue;
+    }
     QueueMeta* m = a.qs.meta + (q % a.qs.Q);
     const unsigned long long p = atomicAdd(&m->tail, 1ull);
     const unsigned lap = (unsigned)(p >> a.qs.cap_log2);
@@ -335,10 +396,12 @@ __global__ void batch_init_kernel(BatchArgs a) {
         ((unsigned long long)(2u * lap + 1u) << 32) | (unsigned)(s_off[q] + a.desc[q].src);
     atomicAdd(&m->count, 1);
     a.inflight[q * kCounterStride] = 1 + a.hdr->phantom;
-    a.qstatus[q] = 0;
   }
   if (tid == 0) {
     a.ctl->remaining = nq;
+    a.ctl->next_q = window;
+    a.ctl->active = window;
+    a.ctl->active_labels = s_off[window];
     a.ctl->stop = 0;
     a.ctl->status = 0;
     for (int i = 0; i < 8; ++i) a.ctl->ctr[i] = 0;
@@ -412,6 +475,7 @@ struct bfq_batch {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   long long bytes = 0;
+  long long l2_bytes = 0;
   std::vector<void*> allocs;
 
   int alloc(void** p, size_t n) {
@@ -494,9 +558,9 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
   if (!b) return b_invalid("bfq_batch_create: host allocation failed");
   bfq_tune_default(&b->tune);
   if (tune && (tune->cycle_walk_hops < 0 || tune->cycle_walk_hops == 1 ||
-               tune->cycle_walk_hops > (1 << 30))) {
+               tune->cycle_walk_hops > (1 << 30) || tune->batch_budget_klabels < -1)) {
     delete b;
-    return b_invalid("bfq_batch_create: cycle_walk_hops out of range");
+    return b_invalid("bfq_batch_create: cycle_walk_hops or batch_budget_klabels out of range");
   }
   if (tune) {
     if (tune->share_div) b->tune.share_div = tune->share_div;
@@ -507,6 +571,7 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
     if (tune->queues_per_cta) b->tune.queues_per_cta = tune->queues_per_cta;
     b->tune.test_phantom_items = tune->test_phantom_items;
     if (tune->cycle_walk_hops) b->tune.cycle_walk_hops = tune->cycle_walk_hops;
+    b->tune.batch_budget_klabels = tune->batch_budget_klabels;
   }
   long long maxV = 0, maxC = 0;
   for (int i = 0; i < ngraphs; ++i) {
@@ -526,6 +591,9 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  b->l2_bytes = l2;
   const size_t dyn = sizeof(int) * 2 * (max_queries + 1);
   b->dyn_smem = dyn;
   if (dyn > 48 * 1024) {
@@ -646,6 +714,12 @@ int bfq_sssp_batch(bfq_batch_t b, int32_t nq, const int32_t* graph_id, const int
   h->batch_items = b->tune.batch_items;
   h->phantom = b->tune.test_phantom_items;
   h->cyc_walk0 = b->tune.cycle_walk_hops;
+  h->budget = b->tune.batch_budget_klabels < 0 ? (1LL << 62)
+              : b->tune.batch_budget_klabels > 0 ? (long long)b->tune.batch_budget_klabels << 10
+                                                 : b->l2_bytes / 2 / (long long)sizeof(long long);
+  int window = 0;
+  while (window < nq && (window == 0 || (long long)loff[window + 1] <= h->budget)) ++window;
+  h->window = window;
   h->time_limit_ns = b->tune.time_limit_ms * 1000000LL;
   h->spin_limit = b->tune.spin_limit;
   cudaStream_t s = (cudaStream_t)stream;
@@ -688,13 +762,14 @@ int bfq_batch_set_tune(bfq_batch_t b, const bfq_tune* t) {
   if (!b || !t) return b_invalid("bfq_batch_set_tune: null argument");
   if (t->share_div < 0 || t->chunk_batch < 0 || t->chunk_batch > 32 || t->batch_items < 0 ||
       t->batch_items > 32 || t->cycle_walk_hops < 0 || t->cycle_walk_hops == 1 ||
-      t->cycle_walk_hops > (1 << 30))
+      t->cycle_walk_hops > (1 << 30) || t->batch_budget_klabels < -1)
     return b_invalid("bfq_batch_set_tune: parameter out of range");
   if (t->share_div) b->tune.share_div = t->share_div;
   if (t->chunk_batch) b->tune.chunk_batch = t->chunk_batch;
   if (t->batch_items) b->tune.batch_items = t->batch_items;
   if (t->time_limit_ms) b->tune.time_limit_ms = t->time_limit_ms;
   if (t->cycle_walk_hops) b->tune.cycle_walk_hops = t->cycle_walk_hops;
+  b->tune.batch_budget_klabels = t->batch_budget_klabels;
   return BFQ_OK;
 }
 

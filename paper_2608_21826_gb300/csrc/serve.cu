@@ -644,6 +644,11 @@ struct bfq_server {
   // at a time, and smaller requests may pass one that waits for its turn.
   long long large_vertices = 0;
   int large_active = 0;
+  // The other requests are admitted while their labels fit a budget (half
+  // of L2 by default), so the labels being relaxed stay in L2.
+  long long small_budget = 0;
+  long long small_labels = 0;
+  int small_active = 0;
   std::vector<int> free_slots;
   std::map<long long, long long> free_pages;        // start page -> page count
   int64_t next_id = 1;
@@ -700,6 +705,8 @@ struct bfq_server {
     }
     admitted.clear();
     large_active = 0;
+    small_labels = 0;
+    small_active = 0;
     for (auto& rq : pending) {
       auto rec = records.find(rq.id);
       if (rec != records.end()) {
@@ -757,7 +764,12 @@ struct bfq_server {
         if (ad != admitted.end()) {
           free_slots.push_back(ad->second.slot);
           free_run(ad->second.start, ad->second.pages);
-          if (ad->second.large) --large_active;
+          if (ad->second.large) {
+            --large_active;
+          } else {
+            --small_active;
+            small_labels -= ad->second.pages << kPageLog2;
+          }
           admitted.erase(ad);
         }
         auto rec = records.find(id);
@@ -774,11 +786,13 @@ struct bfq_server {
         ServeRequest& rq = pending[i];
         const GraphView& gv = views[rq.graph];
         const bool large = gv.V >= large_vertices;
+        const long long need = ((long long)gv.V + (1 << kPageLog2) - 1) >> kPageLog2;
         if (large && large_active > 0) {
           ++i;
           continue;
         }
-        const long long need = ((long long)gv.V + (1 << kPageLog2) - 1) >> kPageLog2;
+        if (!large && small_active > 0 && small_labels + (need << kPageLog2) > small_budget)
+          break;
         long long start = 0;
         if (!alloc_pages(need, &start)) break;
         const int slot = free_slots.back();
@@ -803,7 +817,12 @@ struct bfq_server {
         __atomic_store_n(&c->seq, cmd_tail + 1, __ATOMIC_RELEASE);
         ++cmd_tail;
         admitted[rq.id] = Admitted{slot, start, need, large};
-        if (large) ++large_active;
+        if (large) {
+          ++large_active;
+        } else {
+          ++small_active;
+          small_labels += need << kPageLog2;
+        }
         pending.erase(pending.begin() + (long)i);
         progressed = true;
         peak_active = std::max<long long>(peak_active, (long long)admitted.size());
@@ -844,6 +863,8 @@ struct bfq_server {
           }
           admitted.clear();
           large_active = 0;
+          small_labels = 0;
+          small_active = 0;
           serve_reset_kernel<<<1024, 256, 0, stream>>>(args);
           cudaMemcpyAsync(&args.ctl->cmd_head, &cmd_tail, sizeof(unsigned), cudaMemcpyHostToDevice,
                           stream);
@@ -926,6 +947,11 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
   sv->large_vertices = std::max<long long>(1LL << 20, (long long)l2 / 4 / (long long)sizeof(long long));
+  {
+    const int k = tune ? tune->batch_budget_klabels : 0;
+    sv->small_budget = k < 0 ? (1LL << 62) : k > 0 ? (long long)k << 10
+                                                   : (long long)l2 / 2 / (long long)sizeof(long long);
+  }
   ServeArgs& a = sv->args;
   a.queues_per_cta = 1;
   a.qs.Q = sv->grid;

@@ -183,3 +183,35 @@ def test_full_batched_workload():
         bfq.bfq_batch_destroy(b)
         for h in handles:
             bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("budget", [-1, 4, 16, 0])
+def test_label_budget_staggers_starts_exactly(budget):
+    """Queries start in order while the running ones' labels fit the budget
+    (4 = 4096 labels: one or two graphs' queries at a time; 0 = half of L2;
+    -1 = all at once); the results do not depend on it, including the
+    planted-cycle queries.  Graphs stay small so the oracle ends quickly
+    on the cycle graph."""
+    mix = Mix(n_graphs=12, vmin=500, vmax=6000, seed=8,
+              tune=bfq.make_tune(batch_budget_klabels=budget))
+    try:
+        rc, st, sel = mix.run()
+        assert rc == bfq.OK
+        for i in sel:
+            _check_query(mix, i, st[i])
+        # a second run on the same handle, in reverse order
+        rc, st2, sel2 = mix.run(sel[::-1])
+        for k, i in enumerate(sel2):
+            assert st2[k] == st[i]
+    finally:
+        mix.close()
+
+
+def test_label_budget_is_validated():
+    g = synth.grid_graph(8, 8, seed=1)
+    h = gpu_util.create(g)
+    try:
+        with pytest.raises(bfq.BfqError):
+            bfq.bfq_batch_create([h], 4, 4 * g.V, bfq.make_tune(batch_budget_klabels=-2))
+    finally:
+        bfq.bfq_graph_destroy(h)
