@@ -133,6 +133,9 @@ __device__ __forceinline__ bool start_queries(const BatchArgs& a, const StageHea
   }
 }
 
+// MIN: relax with atomicMin (the running queries' labels fit in L2 under
+// the label budget); both forms are compiled, capture() picks one.
+template <bool MIN>
 __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_kernel(BatchArgs a) {
   extern __shared__ int s_off[];                // loff[nq+1], coff[nq+1]
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
             cV = d.V;
             ctail = ct.x;
           }
-          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cq_q, ctail, lane, home,
+          if (!relax_multi<kGroups, MIN>(env, 1, cep, cdeg, clab, clb, cV, cq_q, ctail, lane, home,
                                     wc, buf, bufq, nbuf, walk_at) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             timed_out = true;
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       }
       if (timed_out) break;
     }
-    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+    if (!relax_multi<kGroups, MIN>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
                               buf, bufq, nbuf, walk_at) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       timed_out = true;
@@ -440,7 +443,7 @@ __global__ void batch_epilogue_kernel(BatchArgs a) {
 
 int batch_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel, kBlock, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_persistent_kernel<true>, kBlock, 0) !=
       cudaSuccess)
     return 1;
   return n < 1 ? 1 : n;
@@ -476,6 +479,7 @@ struct bfq_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   long long bytes = 0;
   long long l2_bytes = 0;
+  bool relax_min = false;                   // the captured persistent kernel's form
   std::vector<void*> allocs;
 
   int alloc(void** p, size_t n) {
@@ -527,6 +531,15 @@ static size_t stage_layout(int maxq, size_t* off_loff, size_t* off_coff, size_t*
   return o;
 }
 
+// atomicMin relaxation while the label budget keeps the running queries'
+// labels within half of L2.
+static bool relax_min_for(const bfq_batch* b) {
+  const int k = b->tune.batch_budget_klabels;
+  const long long labels = k < 0 ? (1LL << 62) : k > 0 ? (long long)k << 10
+                                                      : b->l2_bytes / 2 / (long long)sizeof(long long);
+  return labels <= b->l2_bytes / 2 / (long long)sizeof(long long);
+}
+
 // Capture reset, init, persistent, epilogue and the two copies into one graph.
 static int capture(bfq_batch* b) {
   BFQ_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -535,7 +548,11 @@ static int capture(bfq_batch* b) {
   const size_t smem_off = sizeof(int) * (b->maxq + 1);
   batch_reset_kernel<<<1024, 256, 0, b->cap_stream>>>(b->args);
   batch_init_kernel<<<2048, 256, smem_off, b->cap_stream>>>(b->args);
-  batch_persistent_kernel<<<b->grid, kBlock, b->dyn_smem, b->cap_stream>>>(b->args);
+  b->relax_min = relax_min_for(b);
+  if (b->relax_min)
+    batch_persistent_kernel<true><<<b->grid, kBlock, b->dyn_smem, b->cap_stream>>>(b->args);
+  else
+    batch_persistent_kernel<false><<<b->grid, kBlock, b->dyn_smem, b->cap_stream>>>(b->args);
   batch_epilogue_kernel<<<2048, 256, smem_off, b->cap_stream>>>(b->args);
   cudaMemcpyAsync(b->qcode_host, b->args.qcode, sizeof(int) * b->maxq, cudaMemcpyDeviceToHost,
                   b->cap_stream);
@@ -597,12 +614,15 @@ int bfq_batch_create(bfq_batch_t* out, const bfq_graph_t* graphs, int32_t ngraph
   const size_t dyn = sizeof(int) * 2 * (max_queries + 1);
   b->dyn_smem = dyn;
   if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(batch_persistent_kernel,
+    cudaError_t e = cudaFuncSetAttribute(batch_persistent_kernel<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batch_persistent_kernel<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__); }
   }
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, kBlock, dyn) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<true>, kBlock, dyn) !=
           cudaSuccess || per_sm < 1)
     per_sm = 1;
   b->grid = sms * per_sm;
@@ -770,6 +790,13 @@ int bfq_batch_set_tune(bfq_batch_t b, const bfq_tune* t) {
   if (t->time_limit_ms) b->tune.time_limit_ms = t->time_limit_ms;
   if (t->cycle_walk_hops) b->tune.cycle_walk_hops = t->cycle_walk_hops;
   b->tune.batch_budget_klabels = t->batch_budget_klabels;
+  if (relax_min_for(b) != b->relax_min) {   // the captured kernel changes form
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    return capture(b);
+  }
   return BFQ_OK;
 }
 

@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
             cV = d.V;
             ctail = ct.x;
           }
-          if (!relax_multi<kGroups>(env, 1, cep, cdeg, clab, clb, cV, cs, ctail, lane, home, wc,
+          if (!relax_multi<kGroups, false>(env, 1, cep, cdeg, clab, clb, cV, cs, ctail, lane, home, wc,
                                     buf, bufq, nbuf, walk_at) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             failed = true;
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
       }
       if (failed) break;
     }
-    if (!relax_multi<kGroups>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+    if (!relax_multi<kGroups, false>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
                               buf, bufq, nbuf, walk_at) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       failed = true;

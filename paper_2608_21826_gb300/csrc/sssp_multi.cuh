@@ -51,8 +51,12 @@ __device__ __forceinline__ bool flush_multi(const MultiEnv& e, int home, unsigne
 
 // Merged relaxation of a mixed batch: lane j owns edges [0, deg_j) at eptr_j
 // of a tail with label lab_j in query q_j, whose labels start at lbase_j in
-// the pool and which has V_j vertices.
-template <int U>
+// the pool and which has V_j vertices.  MIN: one atomicMin per edge lowers
+// the label and claims the in-queue flag (keys are even, so key | 1 is below
+// a label exactly when key is below its key part); for labels that stay in
+// L2, since every atomic dirties its line.  Otherwise load, then
+// compare-and-swap when lower.
+template <int U, bool MIN>
 __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2* eptr, int deg,
                                             long long lab, long long* lbase, int Vq, int q,
                                             int tail, int lane, int home, WarpCounters& wc,
@@ -106,30 +110,40 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
           act[g] = false;
         } else {
           key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
-          cur[g] = ld_relaxed_s64(lb[g] + cw[g].x);
+          if (!MIN) cur[g] = ld_relaxed_s64(lb[g] + cw[g].x);
         }
       }
     }
-    // first compare-and-swap of every group back to back (they overlap);
-    // a failed one retries through lower_label
     long long prev[U];
+    if (MIN) {
 #pragma unroll
-    for (int g = 0; g < U; ++g) {
-      prev[g] = cur[g];
-      if (act[g] && key[g] < label_key(cur[g]))
-        prev[g] = (long long)atomicCAS((unsigned long long*)(lb[g] + cw[g].x),
-                                       (unsigned long long)cur[g],
-                                       (unsigned long long)(key[g] | kQueuedBit));
-      else
-        act[g] = false;
+      for (int g = 0; g < U; ++g) {
+        prev[g] = 0;
+        if (act[g]) cur[g] = atomicMin(lb[g] + cw[g].x, key[g] | kQueuedBit);
+      }
+    } else {
+      // first compare-and-swap of every group back to back (they overlap);
+      // a failed one retries through lower_label
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        prev[g] = cur[g];
+        if (act[g] && key[g] < label_key(cur[g]))
+          prev[g] = (long long)atomicCAS((unsigned long long*)(lb[g] + cw[g].x),
+                                         (unsigned long long)cur[g],
+                                         (unsigned long long)(key[g] | kQueuedBit));
+        else
+          act[g] = false;
+      }
     }
     bool enq[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       enq[g] = false;
       if (act[g]) {
-        const int r = (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
-                                          : lower_label(lb[g] + cw[g].x, key[g], prev[g]);
+        const int r =
+            MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
+                : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
+                                      : lower_label(lb[g] + cw[g].x, key[g], prev[g]);
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
