@@ -441,29 +441,32 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(Serv
           deg = ct.z - ct.y;
           Vq = d.V;
         }
-      } else if ((item >> kPageLog2) >= (unsigned)a.pool_pages ||
-                 (unsigned)a.page_owner[item >> kPageLog2] >= (unsigned)a.max_slots ||
-                 (int)item - a.slots[a.page_owner[item >> kPageLog2]].label_off < 0 ||
-                 (int)item - a.slots[a.page_owner[item >> kPageLog2]].label_off >=
-                     a.slots[a.page_owner[item >> kPageLog2]].V) {
-        serve_bad(a, 4, item);
-        bad = true;
       } else {
-        q = a.page_owner[item >> kPageLog2];
-        const SlotDesc& d = a.slots[q];
-        const int u = (int)item - d.label_off;
-        tail = u;
-        lbase = a.label + d.label_off;
-        lab = label_key((long long)atomicAnd((unsigned long long*)(lbase + u),
-                                             ~(unsigned long long)kQueuedBit));
-        const int beg = __ldg(d.row_ptr + u);
-        deg = __ldg(d.row_ptr + u + 1) - beg;
-        eptr = d.adj + beg;
-        Vq = d.V;
-        if (deg > d.hub_degree) {
-          nch = (deg + d.chunk_edges - 1) / d.chunk_edges;
-          c0 = (q << kChunkIdBits) + __ldg(d.hub_chunk0 + u);
-          deg = 0;
+        // the item is a pool index: its page names the slot (each load once)
+        const unsigned page = item >> kPageLog2;
+        const int po = page < (unsigned)a.pool_pages ? a.page_owner[page] : -1;
+        const SlotDesc* dp = a.slots + ((unsigned)po < (unsigned)a.max_slots ? po : 0);
+        const int loff = dp->label_off, Vd = dp->V;
+        const int u = (int)item - loff;
+        if ((unsigned)po >= (unsigned)a.max_slots || u < 0 || u >= Vd) {
+          serve_bad(a, 4, item);
+          bad = true;
+        } else {
+          q = po;
+          tail = u;
+          lbase = a.label + loff;
+          lab = label_key((long long)atomicAnd((unsigned long long*)(lbase + u),
+                                               ~(unsigned long long)kQueuedBit));
+          const int* rp = dp->row_ptr;
+          const int beg = __ldg(rp + u);
+          deg = __ldg(rp + u + 1) - beg;
+          eptr = dp->adj + beg;
+          Vq = Vd;
+          if (deg > dp->hub_degree) {
+            nch = (deg + dp->chunk_edges - 1) / dp->chunk_edges;
+            c0 = (q << kChunkIdBits) + __ldg(dp->hub_chunk0 + u);
+            deg = 0;
+          }
         }
       }
       if (!bad && (ld_relaxed_s32(&a.qstatus[q]) & (kStNegCycle | kStRange))) {
