@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
       continue;
     }
     idle = 0;
-    wc.deq += (lane == 0) ? (unsigned long long)got : 0ull;
-    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
+    wc.deq += (lane == 0) ? (unsigned)got : 0u;
+    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned)got : 0u;
 
     // decode the lanes' items
     int q = -1, deg = 0, nch = 0, c0 = 0, Vq = 0, tail = 0;
@@ -340,15 +340,15 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_
     if (__shfl_sync(kFullMask, stop, 0)) break;
   }
   if (timed_out && lane == 0) batch_timeout(a);
-  wc.upd = warp_sum_u64(wc.upd);
+  const unsigned long long upd_sum = warp_sum_u64(wc.upd);
   if (lane == 0) {
-    if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], wc.deq);
-    if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], wc.rel);
-    if (wc.upd) atomicAdd(&a.ctl->ctr[kCtrUpd], wc.upd);
-    if (wc.enq) atomicAdd(&a.ctl->ctr[kCtrEnq], wc.enq);
-    if (wc.steal) atomicAdd(&a.ctl->ctr[kCtrSteal], wc.steal);
-    if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], wc.chunk);
-    if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], wc.idle);
+    if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], (unsigned long long)wc.deq);
+    if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], (unsigned long long)wc.rel);
+    if (upd_sum) atomicAdd(&a.ctl->ctr[kCtrUpd], upd_sum);
+    if (wc.enq) atomicAdd(&a.ctl->ctr[kCtrEnq], (unsigned long long)wc.enq);
+    if (wc.steal) atomicAdd(&a.ctl->ctr[kCtrSteal], (unsigned long long)wc.steal);
+    if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], (unsigned long long)wc.chunk);
+    if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], (unsigned long long)wc.idle);
   }
 }
 

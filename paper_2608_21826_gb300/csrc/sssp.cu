@@ -53,7 +53,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
                                              unsigned& walk_at) {
   int total = 0;
   const int excl = warp_excl_scan(deg, lane, &total);
-  wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
+  wc.rel += (lane == 0) ? (unsigned)total : 0u;
   const unsigned V = (unsigned)a.V;
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
       continue;
     }
     idle = 0;
-    wc.deq += (lane == 0) ? (unsigned long long)got : 0ull;
-    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned long long)got : 0ull;
+    wc.deq += (lane == 0) ? (unsigned)got : 0u;
+    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned)got : 0u;
 
     int beg = 0, deg = 0, nch = 0, c0 = 0, tail = 0;
     long long lab = 0;
@@ -358,15 +358,15 @@ __global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_k
   }
   if (timed_out && lane == 0) raise_status(a.ctl, kStTimeout);
 
-  wc.upd = warp_sum_u64(wc.upd);
+  const unsigned long long upd_sum = warp_sum_u64(wc.upd);
   if (lane == 0) {
-    if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], wc.deq);
-    if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], wc.rel);
-    if (wc.upd) atomicAdd(&a.ctl->ctr[kCtrUpd], wc.upd);
-    if (wc.enq) atomicAdd(&a.ctl->ctr[kCtrEnq], wc.enq);
-    if (wc.steal) atomicAdd(&a.ctl->ctr[kCtrSteal], wc.steal);
-    if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], wc.chunk);
-    if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], wc.idle);
+    if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], (unsigned long long)wc.deq);
+    if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], (unsigned long long)wc.rel);
+    if (upd_sum) atomicAdd(&a.ctl->ctr[kCtrUpd], upd_sum);
+    if (wc.enq) atomicAdd(&a.ctl->ctr[kCtrEnq], (unsigned long long)wc.enq);
+    if (wc.steal) atomicAdd(&a.ctl->ctr[kCtrSteal], (unsigned long long)wc.steal);
+    if (wc.chunk) atomicAdd(&a.ctl->ctr[kCtrChunk], (unsigned long long)wc.chunk);
+    if (wc.idle) atomicAdd(&a.ctl->ctr[kCtrIdle], (unsigned long long)wc.idle);
   }
 }
 

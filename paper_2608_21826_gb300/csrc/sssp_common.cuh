@@ -100,8 +100,10 @@ __device__ __forceinline__ int enqueue_warp(const QueueSet& qs, int home, bool a
   return done;
 }
 
+// Per-warp statistics of one launch (32 bits: they stay far below 2^32 per
+// warp; the launch totals are 64-bit).
 struct WarpCounters {
-  unsigned long long deq = 0, rel = 0, upd = 0, enq = 0, steal = 0, chunk = 0, idle = 0;
+  unsigned deq = 0, rel = 0, upd = 0, enq = 0, steal = 0, chunk = 0, idle = 0;
 };
 
 constexpr int kChildBuf = 256;   // claimed children buffered per warp

@@ -64,7 +64,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
                                             unsigned& walk_at) {
   int total = 0;
   const int excl = warp_excl_scan(deg, lane, &total);
-  wc.rel += (lane == 0) ? (unsigned long long)total : 0ull;
+  wc.rel += (lane == 0) ? (unsigned)total : 0u;
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
     long long lab_t[U];
