@@ -9,7 +9,8 @@
 // paper's per-round change count and cross-GPU reduction), when a label with
 // hops >= V is accepted (negative cycle), or on a range error or timeout.
 //
-// Labels are (dist, hops) packed in 64 bits and lowered with atomicMin; the
+// Labels are (dist, hops) packed in 64 bits and lowered with one atomicMin
+// (while the labels fit in L2) or a load and a compare-and-swap; the
 // relaxation test is the one of PARALLEL_RELAX_EDGES (Algorithm 3) applied to
 // the lexicographic label and made atomic (the listing's fetch / compare /
 // put sequence would lose concurrent updates).
