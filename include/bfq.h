@@ -329,10 +329,14 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
  * quarter of the device's L2 (V >= L2 bytes / 32; such a query keeps the GPU
  * busy alone, and two of them evict each other's labels) runs only while no
  * other such request runs, and smaller requests behind it may be admitted
- * while it waits.  The other requests are admitted while their labels fit
- * tune->batch_budget_klabels (default: half of L2), so the labels being
- * relaxed stay in L2; one always runs.  A host thread drives admission and
- * completion.  tune may be NULL. */
+ * while it waits.  Such a large request (also any request over half of the
+ * label budget below) runs alone through the single-query kernel on its
+ * graph's handle: the resident kernel stops between batches, the query
+ * runs, and the resident kernel resumes with its queued work.  So while a
+ * server runs, no other query may use a served graph's handle.  The other
+ * requests are admitted while their labels fit tune->batch_budget_klabels
+ * (default: half of L2), so the labels being relaxed stay in L2; one always
+ * runs.  A host thread drives admission and completion.  tune may be NULL. */
 int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngraphs,
                       int64_t hbm_budget_bytes, int32_t max_slots, const bfq_tune* tune);
 /* Queue a request (thread-safe).  dist / hops: caller-owned device arrays of

@@ -652,6 +652,19 @@ struct bfq_server {
   long long small_budget = 0;
   long long small_labels = 0;
   int small_active = 0;
+  // A large request runs alone through the single-query kernel on its
+  // graph's handle: the resident kernel is stopped between batches (its
+  // queued work stays queued), the query runs, the resident kernel resumes.
+  int solo_state = 0;                    // 0 none, 1 stopping the resident kernel, 2 running
+  ServeRequest solo_rq{};
+  bool stop_requested = false;
+  cudaStream_t side = nullptr;           // writes the stop flag while the kernel runs
+  cudaEvent_t solo_done = nullptr;
+  int32_t* solo_status = nullptr;        // pinned: the solo query's status code
+  int32_t* solo_status_dev = nullptr;
+  int* one_host = nullptr;               // pinned 1, for the stop flag
+  int32_t* solo_scratch = nullptr;       // dist for a request that asked for none
+  long long solo_scratch_n = 0;
   std::vector<int> free_slots;
   std::map<long long, long long> free_pages;        // start page -> page count
   int64_t next_id = 1;
@@ -676,6 +689,12 @@ struct bfq_server {
       th.join();
     }
     if (stream) cudaStreamSynchronize(stream);
+    if (side) cudaStreamSynchronize(side);
+    if (solo_done) cudaEventDestroy(solo_done);
+    if (side) cudaStreamDestroy(side);
+    if (solo_status) cudaFreeHost(solo_status);
+    if (one_host) cudaFreeHost(one_host);
+    if (solo_scratch) cudaFree(solo_scratch);
     if (kernel_done) cudaEventDestroy(kernel_done);
     if (stream) cudaStreamDestroy(stream);
     for (void* p : dev_allocs) cudaFree(p);
@@ -710,6 +729,14 @@ struct bfq_server {
     large_active = 0;
     small_labels = 0;
     small_active = 0;
+    if (solo_state == 1) {
+      auto rec = records.find(solo_rq.id);
+      if (rec != records.end()) {
+        rec->second.status = code;
+        rec->second.t_done = now_ns();
+      }
+      solo_state = 0;
+    }
     for (auto& rq : pending) {
       auto rec = records.find(rq.id);
       if (rec != records.end()) {
@@ -794,6 +821,19 @@ struct bfq_server {
           ++i;
           continue;
         }
+        if (large) {
+          // run it alone through the single-query kernel (see solo_state)
+          solo_rq = rq;
+          solo_state = 1;
+          ++large_active;
+          pending.erase(pending.begin() + (long)i);
+          if (launched && !stop_requested) {
+            cudaMemcpyAsync(&args.ctl->stop, one_host, sizeof(int), cudaMemcpyHostToDevice, side);
+            stop_requested = true;
+          }
+          progressed = true;
+          continue;
+        }
         if (!large && small_active > 0 && small_labels + (need << kPageLog2) > small_budget)
           break;
         long long start = 0;
@@ -844,9 +884,12 @@ struct bfq_server {
         ServeCtl c;
         cudaMemcpy(&c, args.ctl, sizeof(c), cudaMemcpyDeviceToHost);
         // a launch that ran to its time limit without completing anything
-        // while requests were admitted counts as stuck
-        stalled_launches = (completed == completed_at_launch && !admitted.empty())
+        // while requests were admitted counts as stuck (not one stopped for
+        // a large request)
+        stalled_launches = (completed == completed_at_launch && !admitted.empty() &&
+                            !stop_requested)
                                ? stalled_launches + 1 : 0;
+        stop_requested = false;
         if (c.bad_where) {
           bad_where = c.bad_where;
           bad_value = c.bad_value;
@@ -874,7 +917,59 @@ struct bfq_server {
           cudaStreamSynchronize(stream);
         }
       }
-      if (!launched && !admitted.empty() && !stopping) {
+      // the solo query: start it once the resident kernel is down, finish it
+      if (solo_state == 1 && !launched) {
+        const GraphView& gv = views[solo_rq.graph];
+        int32_t* dist = solo_rq.dist;
+        int rc = BFQ_OK;
+        if (!dist) {
+          if (solo_scratch_n < gv.V) {
+            if (solo_scratch) cudaFree(solo_scratch);
+            solo_scratch = nullptr;
+            solo_scratch_n = 0;
+            if (cudaMalloc((void**)&solo_scratch, sizeof(int32_t) * (size_t)gv.V) == cudaSuccess)
+              solo_scratch_n = gv.V;
+            else
+              rc = BFQ_ERR_OOM;
+          }
+          dist = solo_scratch;
+        }
+        if (rc == BFQ_OK)
+          rc = bfq_sssp_async(graphs[solo_rq.graph], solo_rq.src, dist, solo_rq.hops, nullptr,
+                              solo_status_dev, stream);
+        if (rc == BFQ_OK) {
+          cudaMemcpyAsync(solo_status, solo_status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          stream);
+          cudaEventRecord(solo_done, stream);
+          solo_state = 2;
+        } else {
+          auto rec = records.find(solo_rq.id);
+          if (rec != records.end()) {
+            rec->second.status = rc;
+            rec->second.t_done = now_ns();
+          }
+          ++completed;
+          --large_active;
+          solo_state = 0;
+        }
+        progressed = true;
+      }
+      if (solo_state == 2) {
+        const cudaError_t se = cudaEventQuery(solo_done);
+        if (se != cudaErrorNotReady) {
+          auto rec = records.find(solo_rq.id);
+          if (rec != records.end()) {
+            rec->second.status = se == cudaSuccess ? *solo_status : BFQ_ERR_CUDA;
+            rec->second.t_done = now_ns();
+          }
+          if (se != cudaSuccess) cuda_error = (int)se;
+          ++completed;
+          --large_active;
+          solo_state = 0;
+          progressed = true;
+        }
+      }
+      if (!launched && !admitted.empty() && !stopping && solo_state == 0) {
         completed_at_launch = completed;
         cudaMemsetAsync(&args.ctl->stop, 0, sizeof(int), stream);
         serve_kernel<<<grid, kBlock, 0, stream>>>(args);
@@ -882,8 +977,8 @@ struct bfq_server {
         launched = true;
         ++relaunches;
       }
-      if (stopping && admitted.empty() && pending.empty()) break;
-      if (stopping && !launched) break;
+      if (stopping && admitted.empty() && pending.empty() && solo_state == 0) break;
+      if (stopping && !launched && solo_state == 0) break;
       if (!progressed) {
         cv.wait_for(lk, std::chrono::microseconds(20));
       }
@@ -949,11 +1044,13 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   sv->grid = sms * per_sm;
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-  sv->large_vertices = std::max<long long>(1LL << 20, (long long)l2 / 4 / (long long)sizeof(long long));
   {
     const int k = tune ? tune->batch_budget_klabels : 0;
     sv->small_budget = k < 0 ? (1LL << 62) : k > 0 ? (long long)k << 10
                                                    : (long long)l2 / 2 / (long long)sizeof(long long);
+    // large: labels over a quarter of L2, or over half of the budget
+    sv->large_vertices = std::min<long long>((long long)l2 / 4 / (long long)sizeof(long long),
+                                             std::max<long long>(1, sv->small_budget / 2));
   }
   ServeArgs& a = sv->args;
   a.queues_per_cta = 1;
@@ -998,6 +1095,7 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   S_TRY(sv->dalloc((void**)&a.tq.meta, sizeof(QueueMeta)));
   S_TRY(sv->dalloc((void**)&a.tq.slots, sizeof(unsigned long long) * ((size_t)1 << a.tq.cap_log2)));
   S_TRY(sv->dalloc((void**)&a.ctl, sizeof(ServeCtl)));
+  S_TRY(sv->dalloc((void**)&sv->solo_status_dev, sizeof(int32_t)));
 #undef S_TRY
 #define S_CUDA(x) do { cudaError_t e__ = (x); if (e__ != cudaSuccess) { int r__ = cuda_fail(e__, #x, __FILE__, __LINE__); delete sv; return r__; } } while (0)
   S_CUDA(cudaHostAlloc((void**)&sv->cmd_host, sizeof(ServeCmd) * sv->ring, cudaHostAllocMapped));
@@ -1014,6 +1112,11 @@ int bfq_server_create(bfq_server_t* out, const bfq_graph_t* graphs, int32_t ngra
   S_CUDA(cudaMemset(a.inflight, 0, sizeof(int) * kCounterStride * max_slots));
   S_CUDA(cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking));
   S_CUDA(cudaEventCreateWithFlags(&sv->kernel_done, cudaEventDisableTiming));
+  S_CUDA(cudaStreamCreateWithFlags(&sv->side, cudaStreamNonBlocking));
+  S_CUDA(cudaEventCreateWithFlags(&sv->solo_done, cudaEventDisableTiming));
+  S_CUDA(cudaMallocHost((void**)&sv->solo_status, sizeof(int32_t)));
+  S_CUDA(cudaMallocHost((void**)&sv->one_host, sizeof(int)));
+  *sv->one_host = 1;
   serve_reset_kernel<<<1024, 256, 0, sv->stream>>>(a);
   S_CUDA(cudaGetLastError());
   S_CUDA(cudaStreamSynchronize(sv->stream));

@@ -114,3 +114,49 @@ def test_arrivals_during_running_queries_and_idle_gaps():
         bfq.bfq_server_destroy(sv)
         for h in handles:
             bfq.bfq_graph_destroy(h)
+
+
+def test_large_requests_run_alone_between_small_ones():
+    """Requests over half of the label budget (here 32K labels, so graphs of
+    16K+ vertices) run alone through the single-query kernel while the
+    resident kernel is stopped and later resumed; small requests submitted
+    around them still complete, and every result equals the solo run."""
+    import torch
+    graphs, queries, handles = _setup(n_graphs=6, seed=33, vmax=5000)
+    big = [synth.grid_graph(160, 160, seed=9), synth.workload_rmat(15)]
+    bh = [gpu_util.create(g) for g in big]
+    all_g = list(graphs) + big
+    all_h = list(handles) + bh
+    sv = bfq.bfq_server_create(all_h, 1 << 30, 64, bfq.make_tune(batch_budget_klabels=32))
+    try:
+        reqs = []
+        k = 0
+        for gi, s in queries:
+            reqs.append((int(gi), int(s)))
+            if k % 5 == 0:                                 # a large one every few
+                bi = len(graphs) + (k // 5) % 2
+                reqs.append((bi, int(all_g[bi].sources[k % len(all_g[bi].sources)])))
+            k += 1
+        bufs = [torch.full((all_g[gi].V,), -3, dtype=torch.int32, device="cuda")
+                for gi, _ in reqs]
+        torch.cuda.synchronize()
+        ids = [bfq.bfq_server_submit(sv, gi, s, bufs[i]) for i, (gi, s) in enumerate(reqs)]
+        sts = [bfq.bfq_server_wait(sv, rid, 60000) for rid in ids]
+        assert bfq.bfq_server_stats(sv)["completed"] == len(reqs)
+    finally:
+        bfq.bfq_server_destroy(sv)
+    try:
+        for (gi, s), st, d in zip(reqs, sts, bufs):
+            sst, sd, _, _ = gpu_util.run(all_h[gi], all_g[gi].V, s)
+            assert st == sst, (gi, s)
+            if st == bfq.OK:
+                assert np.array_equal(d.cpu().numpy(), sd), (gi, s)
+        for bi in (len(graphs), len(graphs) + 1):
+            g = all_g[bi]
+            s = int(g.sources[0])
+            ost, od, _, _ = oracle.spfa(g.row_ptr, g.col, g.w, s)
+            sst, sd, _, _ = gpu_util.run(all_h[bi], g.V, s)
+            assert sst == ost and np.array_equal(sd, od)
+    finally:
+        for h in all_h:
+            bfq.bfq_graph_destroy(h)
