@@ -279,8 +279,9 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7, tune=None):
     all_g = list(graphs) + [g23]
     all_h = list(handles) + [h23]
     rng = np.random.default_rng(seed)
-    # output buffers: a ring per graph, a buffer reused once its request is done
-    ring = 16
+    # output buffers: a ring per graph, a buffer reused once its request is
+    # done (64 deep, so the client itself rarely waits on a slow request)
+    ring = 64
     bufs = [[torch.empty(g.V, dtype=torch.int32, device=dev) for _ in range(ring)] for g in all_g]
     torch.cuda.synchronize()
     budget = 32 * 700_000_000              # label pool of 700M labels (22.4 GB)
