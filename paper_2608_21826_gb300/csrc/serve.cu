@@ -971,6 +971,8 @@ struct bfq_server {
       }
       if (!launched && !admitted.empty() && !stopping && solo_state == 0) {
         completed_at_launch = completed;
+        // a stop written from the side stream must land before it is cleared
+        cudaStreamSynchronize(side);
         cudaMemsetAsync(&args.ctl->stop, 0, sizeof(int), stream);
         serve_kernel<<<grid, kBlock, 0, stream>>>(args);
         cudaEventRecord(kernel_done, stream);
