@@ -66,3 +66,29 @@ def test_host_side_checks_without_gpu():
     assert rc == bfq.ERR_INVALID and "batch_items" in bfq.last_error()
     with pytest.raises(bfq.BfqError):
         bfq.bfq_sssp(None, 0, None)
+
+
+def test_tune_struct_layout_matches_the_header():
+    """bfq_tune_default clears exactly sizeof(bfq_tune) bytes: a sentinel
+    after the Python struct stays intact, and the fields land where the
+    binding expects them (defaults of the last fields)."""
+    n = ctypes.sizeof(bfq.Tune)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    assert bfq.lib().bfq_tune_default(ctypes.cast(buf, ctypes.POINTER(bfq.Tune))) == bfq.OK
+    assert all(b == 0xAB for b in bytes(buf)[n:])
+    t = bfq.Tune.from_buffer_copy(bytes(buf)[:n])
+    assert t.cycle_walk_hops == 64 and t.relax_atomic == bfq.RELAX_AUTO
+    assert t.neg_cycle_mode == bfq.NEG_CYCLE_STOP and t.batch_budget_klabels == 0
+    assert t.share_div == 2 and t.chunk_batch == 4 and t.l2_persist_pct == 0
+
+
+@pytest.mark.parametrize("field,value", [("relax_atomic", 3), ("neg_cycle_mode", 2),
+                                         ("cycle_walk_hops", 1), ("l2_persist_pct", 101)])
+def test_bad_tunes_rejected_before_any_device_work(field, value):
+    import numpy as np
+    h = ctypes.c_void_p()
+    rp = np.array([0, 0], np.int32)
+    bad = bfq.make_tune(**{field: value})
+    rc = bfq.lib().bfq_graph_create(ctypes.byref(h), 1, 0, rp.ctypes.data, None, None, 0,
+                                    ctypes.byref(bad), None)
+    assert rc == bfq.ERR_INVALID
