@@ -417,8 +417,28 @@ def queue_leg(dev, n_ops=10_000_000):
         finally:
             bfq.bfq_queue_destroy(q)
         res[name] = best
-    return {"ops": n_ops, "variants": res,
-            "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts"}
+    # measured L2 atomic peaks, the denominators of the queue numbers
+    peaks = {}
+    for mode, key in ((0, "distinct_address_add"), (1, "same_address_ticket_add"),
+                      (2, "same_address_warp_cas")):
+        best = 0.0
+        for grid, block in shapes:
+            ms, tot = bfq.bfq_atomic_bench(mode, n_ops, grid, block)
+            if tot == n_ops and ms > 0:
+                best = max(best, n_ops / (ms / 1e3))
+        peaks[key] = best
+    frac = {}
+    if peaks["same_address_ticket_add"] > 0:
+        for name in ("bq", "bwd"):
+            if "enqdeq" in res.get(name, {}):
+                frac[name] = res[name]["enqdeq"]["ops_per_s"] / peaks["same_address_ticket_add"]
+    if peaks["same_address_warp_cas"] > 0 and "enqdeq" in res.get("bq_warp", {}):
+        frac["bq_warp"] = res["bq_warp"]["enqdeq"]["ops_per_s"] / peaks["same_address_warp_cas"]
+    return {"ops": n_ops, "variants": res, "atomic_peaks_ops_per_s": peaks,
+            "enqdeq_frac_of_atomic_peak": frac,
+            "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts; "
+                    "per-thread BQ/BWD against one-address ticket adds, the warp-aggregated "
+                    "queue against one-address warp compare-and-swap"}
 
 
 def rounds_leg(h, srcs, dist_t, flush, stream, m_per_query, queue_kernel_ms):

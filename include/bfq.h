@@ -391,6 +391,18 @@ int bfq_queue_mixed(bfq_queue_t q, const int32_t* items, int64_t n_enq,
                     int64_t* enq_pos, int32_t* out, int64_t n_deq,
                     int64_t* deq_pos, int32_t grid, int32_t block,
                     void* stream);
+/* L2 atomic throughput on this device (the measured denominator of the
+ * queue benchmark; the paper has no counterpart): n_ops atomics by grid x
+ * block threads.  mode 0: each thread adds to its own 8-byte counter
+ * (distinct addresses); 1: every thread adds to one counter and uses the
+ * returned value (a ticket); 2: one lane per warp moves one counter by 32
+ * with a compare-and-swap loop (n_ops a multiple of 32, counted as 32 per
+ * success).  *ms_out (nullable) receives the CUDA-event time of the launch
+ * and *total_out (nullable) the sum of the counters (== n_ops).  Allocates
+ * and frees its counters; synchronises `stream`. */
+int bfq_atomic_bench(int32_t mode, int64_t n_ops, int32_t grid, int32_t block,
+                     double* ms_out, int64_t* total_out, void* stream);
+
 /* Read head, tail and count (host pointers, each nullable) and the queue's
  * error word; synchronises `stream`.  Returns BFQ_OK or BFQ_ERR_TIMEOUT if a
  * ticket wait of an earlier launch ran out. */

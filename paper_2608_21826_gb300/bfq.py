@@ -109,6 +109,8 @@ _SIGNATURES = {
     "bfq_queue_mixed": ([_VP, _VP, _I64, _VP, _VP, _I64, _VP, _I32, _I32, _VP], ctypes.c_int),
     "bfq_queue_state": ([_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                          ctypes.POINTER(_I64), _VP], ctypes.c_int),
+    "bfq_atomic_bench": ([_I32, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(_I64), _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -472,3 +474,11 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def bfq_atomic_bench(mode: int, n_ops: int, grid: int, block: int, stream=None):
+    """L2 atomic throughput microbenchmark; returns (ms, total)."""
+    ms, tot = ctypes.c_double(), _I64()
+    _check(lib().bfq_atomic_bench(int(mode), int(n_ops), int(grid), int(block),
+                                  ctypes.byref(ms), ctypes.byref(tot), _stream(stream)))
+    return ms.value, tot.value

@@ -226,7 +226,80 @@ static int launch_ok(const char* what) {
   return BFQ_OK;
 }
 
+// L2 atomic throughput: mode 0 = every thread adds to its own counter
+// (distinct addresses), 1 = every thread adds to one counter and uses the old
+// value (as a ticket), 2 = one lane per warp moves one counter by 32 with a
+// compare-and-swap loop (the exact-count reservation of the warp-aggregated
+// queue), counting 32 operations per success.  Totals land in ctr.
+__global__ void atomic_bench_kernel(unsigned long long* ctr, long long n_ops, int mode,
+                                    unsigned long long* sink) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long acc = 0;
+  if (mode == 0) {
+    for (long long i = tid; i < n_ops; i += nth) acc += atomicAdd(&ctr[tid], 1ull);
+  } else if (mode == 1) {
+    for (long long i = tid; i < n_ops; i += nth) acc ^= atomicAdd(&ctr[0], 1ull);
+  } else {
+    const int lane = threadIdx.x & 31;
+    const long long warp = tid >> 5, nw = nth >> 5;
+    for (long long i = warp; i < n_ops / 32; i += nw) {
+      if (lane == 0) {
+        unsigned long long old = ld_relaxed_u64(&ctr[0]);
+        for (;;) {
+          const unsigned long long seen = atomicCAS(&ctr[0], old, old + 32ull);
+          if (seen == old) break;
+          old = seen;
+        }
+        acc += old;
+      }
+      __syncwarp();
+    }
+  }
+  if (acc == 0x5eed5eed5eed5eedull) *sink = acc;   // keeps the results live
+}
+
 extern "C" {
+
+static int check_launch(int32_t grid, int32_t block, int64_t n);
+
+int bfq_atomic_bench(int32_t mode, int64_t n_ops, int32_t grid, int32_t block,
+                     double* ms_out, int64_t* total_out, void* stream) {
+  if (mode < 0 || mode > 2) return q_invalid("bfq_atomic_bench: mode must be 0, 1 or 2");
+  int rc = check_launch(grid, block, n_ops);
+  if (rc) return rc;
+  if (mode == 2 && n_ops % 32) return q_invalid("bfq_atomic_bench: mode 2 needs n_ops % 32 == 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nctr = (size_t)grid * (size_t)block + 1;
+  unsigned long long* ctr = nullptr;
+  BFQ_CUDA_TRY(cudaMalloc((void**)&ctr, sizeof(unsigned long long) * nctr));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * nctr, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) {
+    atomic_bench_kernel<<<grid, block, 0, s>>>(ctr, n_ops, mode, ctr + nctr - 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  long long total = 0;
+  if (e == cudaSuccess && total_out) {
+    std::vector<unsigned long long> h(nctr - 1);
+    e = cudaMemcpy(h.data(), ctr, sizeof(unsigned long long) * (nctr - 1), cudaMemcpyDeviceToHost);
+    for (unsigned long long v : h) total += (long long)v;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ctr);
+  if (e != cudaSuccess) return cuda_fail(e, "bfq_atomic_bench", __FILE__, __LINE__);
+  if (ms_out) *ms_out = ms;
+  if (total_out) *total_out = total;
+  return BFQ_OK;
+}
 
 int bfq_queue_create(bfq_queue_t* out, int64_t capacity, int32_t variant) {
   if (!out) return q_invalid("bfq_queue_create: out is null");

@@ -120,3 +120,16 @@ def test_mixed(variant, grid):
         assert st == bfq.OK and count == 0 and head == tail == n_enq
     finally:
         bfq.bfq_queue_destroy(q)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_atomic_bench_counts_every_operation(mode):
+    n = 1 << 20
+    ms, tot = bfq.bfq_atomic_bench(mode, n, 152, 256)
+    assert tot == n and ms > 0
+
+
+def test_atomic_bench_rejects_bad_arguments():
+    for args in ((3, 1024, 8, 64), (0, 1024, 8, 48), (2, 1000, 8, 64), (0, -1, 8, 64)):
+        with pytest.raises(bfq.BfqError):
+            bfq.bfq_atomic_bench(*args)
