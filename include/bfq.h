@@ -332,7 +332,8 @@ int bfq_batch_autotune(bfq_batch_t b, int32_t nq, const int32_t* graph_id,
  * while it waits.  Such a large request (also any request over half of the
  * label budget below) runs alone through the single-query kernel on its
  * graph's handle: the resident kernel stops between batches, the query
- * runs, and the resident kernel resumes with its queued work.  So while a
+ * runs, and the resident kernel resumes with its queued work.  It runs with
+ * the handle's own run-time parameters (bfq_graph_set_tune).  So while a
  * server runs, no other query may use a served graph's handle.  The other
  * requests are admitted while their labels fit tune->batch_budget_klabels
  * (default: half of L2), so the labels being relaxed stay in L2; one always
