@@ -164,11 +164,18 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
+    """Hash of the persistent kernel's code (comments and blank lines left
+    out, so a comment edit does not invalidate the committed counters)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("sssp.cu", "sssp_common.cuh", "bfq_device.cuh", "bfq_internal.h"):
-        with open(os.path.join(ROOT, "paper_2608_21826_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2608_21826_gb300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 
