@@ -283,6 +283,8 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7, tune=None):
     from paper_2608_21826_gb300 import bfq, synth
     g23 = synth.workload_rmat(23)
     h23 = bfq.bfq_graph_create(g23.row_ptr, g23.col, g23.w)
+    # large requests run alone on this handle: tune it (untimed)
+    bfq.bfq_autotune(h23, [int(x) for x in g23.sources])
     all_g = list(graphs) + [g23]
     all_h = list(handles) + [h23]
     rng = np.random.default_rng(seed)
