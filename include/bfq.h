@@ -124,6 +124,13 @@ typedef struct bfq_tune {
                                admits requests below its large-request size
                                by the same budget.  0 = half of L2 (8-byte
                                labels); -1 = no budget                      */
+  int32_t kernel_ctas;      /* register form of bfq_sssp's persistent kernel:
+                               4 = built for 4 CTAs per SM (64 registers per
+                               thread), 3 = built for 3 (80 registers: fewer
+                               spills, fewer warps; it runs on a smaller
+                               grid, never above ctas_per_sm).  0 = auto: 3
+                               when E < 8 V, else 4.  Results are the same
+                               either way; bfq_autotune tries both.         */
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
@@ -278,11 +285,12 @@ int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
                      int64_t E, int32_t src, int32_t* dist, int32_t* hops,
                      int32_t* status_dev, void* stream);
 
-/* Pick the run-time parameters (share_div, chunk_batch, batch_items) that
- * make the queries from srcs[0..n) (host array) fastest on g, keep them on
- * the handle and copy them to *out (nullable).  Tries a fixed grid of
- * candidates, timing each with CUDA events; allocates one int32[V] scratch
- * array for the duration.  Synchronises `stream`. */
+/* Pick the run-time parameters (share_div, chunk_batch, batch_items, then
+ * kernel_ctas) that make the queries from srcs[0..n) (host array) fastest on
+ * g, keep them on the handle and copy them to *out (nullable).  Tries a fixed
+ * grid of candidates in the handle's register form, then the other form at
+ * the best of them, timing each with CUDA events; allocates one int32[V]
+ * scratch array for the duration.  Synchronises `stream`. */
 int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
 
 /* ---- batched queries: many sources over many resident graphs in one

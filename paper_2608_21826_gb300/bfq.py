@@ -36,7 +36,8 @@ class Tune(ctypes.Structure):
                 ("l2_persist_pct", ctypes.c_int32), ("test_phantom_items", ctypes.c_int32),
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
                 ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
-                ("relax_atomic", ctypes.c_int32), ("batch_budget_klabels", ctypes.c_int32)]
+                ("relax_atomic", ctypes.c_int32), ("batch_budget_klabels", ctypes.c_int32),
+                ("kernel_ctas", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

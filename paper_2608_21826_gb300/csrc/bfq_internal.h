@@ -54,6 +54,9 @@ struct SsspArgs {
   int mark_neg_inf;             // 1: resolve negative cycles to minus infinity
   unsigned cyc_walk0;           // first cycle-walk threshold (hops); records from half
   int relax_min;                // 1: relax with one atomicMin (labels fit in L2)
+  int wide;                     // 1: the 80-register build (3 CTAs per SM), else 64
+  int q_alloc;                  // sub-queues allocated (qs.Q of them serve this run;
+  int cq_alloc;                 //   a reset clears all); 0: as many as qs.Q / cq.Q
 };
 
 struct LaunchShape {
@@ -72,7 +75,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
   } while (0)
 
 // Kernels launchers (sssp.cu)
-int sssp_max_ctas_per_sm(int block);
+int sssp_max_ctas_per_sm(int block, int wide);
 // init, persistent run (bracketed by ev0/ev1 when given), epilogue, pred.
 // l2win (nullable): L2 access-policy window attached to the persistent launch.
 cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape run_shape,

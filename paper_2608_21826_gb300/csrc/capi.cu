@@ -58,7 +58,11 @@ struct bfq_graph {
   unsigned long long* scratch = nullptr;   // [2] reached-edge reduction
   int32_t* status_host = nullptr;          // pinned
   LaunchShape init_shape{};
-  LaunchShape run_shape{};
+  LaunchShape run_shape{};                     // the workspace's shape (narrow form)
+  int sms = 0;
+  int per_sm_wide = 0;                         // CTAs per SM of the wide form
+  LaunchShape last_shape{};                    // the last run's shape and
+  int last_queues = 0;                         //   vertex sub-queues (stats)
   long long bytes = 0;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the persistent kernel
@@ -158,6 +162,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   out->neg_cycle_mode = in->neg_cycle_mode;
   if (in->cycle_walk_hops) out->cycle_walk_hops = in->cycle_walk_hops;
   out->relax_atomic = in->relax_atomic;
+  out->kernel_ctas = in->kernel_ctas;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 in this build");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -173,7 +178,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32 ||
       (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK) ||
       out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30) ||
-      out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_CAS)
+      out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_CAS ||
+      (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4))
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -275,9 +281,12 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   G_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device));
   g->l2_bytes = l2;
   const int block = g->tune.threads_per_cta;
-  int per_sm = sssp_max_ctas_per_sm(block);
+  int per_sm = sssp_max_ctas_per_sm(block, 0);
   if (g->tune.ctas_per_sm > 0) per_sm = std::min(per_sm, g->tune.ctas_per_sm);
   g->run_shape = {sms * per_sm, block};
+  g->sms = sms;
+  // the wide form fits fewer CTAs: it runs on a prefix of the sub-queues
+  g->per_sm_wide = std::min(per_sm, sssp_max_ctas_per_sm(block, 1));
   g->init_shape = {sms * 4, 256};
 
   // workspace: labels (with in-queue flags), vertex and chunk sub-queues
@@ -326,6 +335,13 @@ int bfq_graph_destroy(bfq_graph_t g) {
 
 int64_t bfq_graph_device_bytes(bfq_graph_t g) { return g ? g->bytes : 0; }
 
+// Register form of the persistent kernel: 80 registers (3 CTAs per SM) by
+// default below an average out-degree of 8, where queue operations take a
+// larger share of each warp step.
+static int wide_form(bfq_graph_t g, const bfq_tune& t) {
+  return t.kernel_ctas == 3 ? 1 : t.kernel_ctas == 4 ? 0 : g->E < 8LL * g->V ? 1 : 0;
+}
+
 static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
                           int32_t* pred) {
   SsspArgs a{};
@@ -358,7 +374,20 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.relax_min = g->tune.relax_atomic == BFQ_RELAX_MIN ? 1
                 : g->tune.relax_atomic == BFQ_RELAX_CAS ? 0
                 : (long long)sizeof(long long) * g->V <= g->l2_bytes / 2 ? 1 : 0;
+  a.wide = wide_form(g, g->tune);
+  a.q_alloc = g->qs.Q;
+  a.cq_alloc = g->cq.Q;
+  if (a.wide) {
+    // a smaller grid on a prefix of the sub-queues (the init kernel resets
+    // all of them after any run that did not end cleanly)
+    a.qs.Q = g->sms * g->per_sm_wide * g->tune.queues_per_cta;
+    if (g->n_chunks > 0) a.cq.Q = g->sms * g->per_sm_wide;
+  }
   return a;
+}
+
+static LaunchShape shape_for(bfq_graph_t g, const SsspArgs& a) {
+  return a.wide ? LaunchShape{g->sms * g->per_sm_wide, g->run_shape.block} : g->run_shape;
 }
 
 // L2 persistence for the label array (Sec. IV's L2 set-aside sweep): set
@@ -407,7 +436,9 @@ int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int
     g->release_l2();
   }
   SsspArgs a = make_args(g, src, dist, hops, pred);
-  BFQ_CUDA_TRY(launch_sssp(a, g->init_shape, g->run_shape, status_dev, g->ev0, g->ev1, s, win));
+  g->last_shape = shape_for(g, a);
+  g->last_queues = a.qs.Q;
+  BFQ_CUDA_TRY(launch_sssp(a, g->init_shape, g->last_shape, status_dev, g->ev0, g->ev1, s, win));
   return BFQ_OK;
 }
 
@@ -492,9 +523,10 @@ int bfq_get_stats(bfq_graph_t g, bfq_stats* out) {
   out->reached = (int64_t)red[1];
   out->V = g->V;
   out->E = g->E;
-  out->grid = g->run_shape.grid;
-  out->block = g->run_shape.block;
-  out->queues = g->qs.Q;
+  const LaunchShape sh = g->last_shape.grid ? g->last_shape : g->run_shape;
+  out->grid = sh.grid;
+  out->block = sh.block;
+  out->queues = g->last_queues ? g->last_queues : g->qs.Q;
   out->queue_capacity = 1 << g->qs.cap_log2;
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) out->kernel_ms = ms;
@@ -516,27 +548,36 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
   bfq_tune best_t = keep;
   float best = -1.f;
   int rc = BFQ_OK;
+  // device time of the second of two passes over the sources on g->tune
+  auto time_it = [&]() {
+    float total = 0.f;
+    for (int rep = 0; rep < 2 && rc == BFQ_OK; ++rep) {
+      for (int i = 0; i < n && rc == BFQ_OK; ++i) {
+        int st = bfq_sssp(g, srcs[i], dist, nullptr, nullptr, stream);
+        if (st < 0) rc = st;
+        float ms = 0.f;
+        if (rep == 1 && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) total += ms;
+      }
+    }
+    if (rc == BFQ_OK && (best < 0.f || total < best)) {
+      best = total;
+      best_t = g->tune;
+    }
+  };
   for (int si : kShare)
     for (int ci : kChunk)
       for (int ii : kItems) {
         g->tune.share_div = si;
         g->tune.chunk_batch = ci;
         g->tune.batch_items = ii;
-        float total = 0.f;
-        for (int rep = 0; rep < 2 && rc == BFQ_OK; ++rep) {
-          for (int i = 0; i < n && rc == BFQ_OK; ++i) {
-            int st = bfq_sssp(g, srcs[i], dist, nullptr, nullptr, stream);
-            if (st < 0) rc = st;
-            float ms = 0.f;
-            if (rep == 1 && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) total += ms;
-          }
-        }
+        time_it();
         if (rc != BFQ_OK) break;
-        if (best < 0.f || total < best) {
-          best = total;
-          best_t = g->tune;
-        }
       }
+  if (rc == BFQ_OK) {               // the other register form, at the best parameters
+    g->tune = best_t;
+    g->tune.kernel_ctas = wide_form(g, best_t) ? 4 : 3;
+    time_it();
+  }
   cudaStreamSynchronize(s);
   cudaFree(dist);
   g->tune = (rc == BFQ_OK) ? best_t : keep;

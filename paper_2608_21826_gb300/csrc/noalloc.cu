@@ -160,7 +160,7 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   if (rc != BFQ_OK) return rc;
   int sms = 0;
   BFQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const LaunchShape run{sms * sssp_max_ctas_per_sm(256), 256};
+  const LaunchShape run{sms * sssp_max_ctas_per_sm(256, 0), 256};
   const LaunchShape init{sms * 4, 256};
   cudaStream_t s = (cudaStream_t)stream;
 

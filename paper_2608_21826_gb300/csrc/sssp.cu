@@ -230,10 +230,16 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
   return true;
 }
 
-// MIN: lower labels with one atomicMin per edge (see relax_merged); both
-// forms are compiled and the launcher picks one per run.
-template <bool MIN>
-__global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) sssp_persistent_kernel(SsspArgs a) {
+// MIN: lower labels with one atomicMin per edge (see relax_merged).  CTAS:
+// the CTAs per SM the register budget is sized for: kCtasNarrow (64
+// registers per thread, more warps in flight) or kCtasWide (80 registers,
+// fewer spills; faster on low-degree graphs, whose warps spend more of each
+// step in queue operations).  All four forms are compiled; the launcher
+// picks one per run.
+constexpr int kCtasNarrow = BFQ_MIN_CTAS_PER_SM;
+constexpr int kCtasWide = 3;
+template <bool MIN, int CTAS>
+__global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs a) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -410,17 +416,22 @@ __global__ void sssp_init_kernel(SsspArgs a) {
   for (long long v = tid; v < a.V; v += nth)
     a.label[v] = (v == a.src) ? (pack_label(0, 0) | kQueuedBit) : kInfLabel;
   if (dirty) {
-    const long long nslots = (long long)a.qs.Q << a.qs.cap_log2;
+    // every allocated sub-queue, also those a run of the other register form
+    // used: a clean run leaves all of its sub-queues empty, so after this
+    // reset the ones outside qs.Q / cq.Q stay empty for later runs
+    const int q_all = a.q_alloc > 0 ? a.q_alloc : a.qs.Q;
+    const int cq_all = a.cq_alloc > 0 ? a.cq_alloc : a.cq.Q;
+    const long long nslots = (long long)q_all << a.qs.cap_log2;
     for (long long i = tid; i < nslots; i += nth)
       a.qs.slots[i] = (i == 0) ? ((1ull << 32) | (unsigned)a.src) : 0ull;
-    const long long ncslots = (long long)a.cq.Q << a.cq.cap_log2;
+    const long long ncslots = (long long)cq_all << a.cq.cap_log2;
     for (long long i = tid; i < ncslots; i += nth) a.cq.slots[i] = 0ull;
-    for (long long q = tid; q < a.qs.Q; q += nth) {
+    for (long long q = tid; q < q_all; q += nth) {
       a.qs.meta[q].count = (q == 0) ? 1 : 0;
       a.qs.meta[q].head = 0;
       a.qs.meta[q].tail = (q == 0) ? 1 : 0;
     }
-    for (long long q = tid; q < a.cq.Q; q += nth) {
+    for (long long q = tid; q < cq_all; q += nth) {
       a.cq.meta[q].count = 0;
       a.cq.meta[q].head = 0;
       a.cq.meta[q].tail = 0;
@@ -519,13 +530,46 @@ __global__ void queue_reset_kernel(QueueSet qs) {
   }
 }
 
+// The persistent kernel in the form a.relax_min / a.wide name, with the L2
+// access-policy window as a launch attribute when one is given.
+template <bool MIN, int CTAS>
+cudaError_t launch_persistent_as(const SsspArgs& a, LaunchShape sh, cudaStream_t s,
+                                 const cudaAccessPolicyWindow* l2win) {
+  if (!l2win) {
+    sssp_persistent_kernel<MIN, CTAS><<<sh.grid, sh.block, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(sh.grid);
+  cfg.blockDim = dim3(sh.block);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+  attr[0].val.accessPolicyWindow = *l2win;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<MIN, CTAS>, a);
+}
+
+cudaError_t launch_persistent(const SsspArgs& a, LaunchShape sh, cudaStream_t s,
+                              const cudaAccessPolicyWindow* l2win) {
+  if (a.wide)
+    return a.relax_min ? launch_persistent_as<true, kCtasWide>(a, sh, s, l2win)
+                       : launch_persistent_as<false, kCtasWide>(a, sh, s, l2win);
+  return a.relax_min ? launch_persistent_as<true, kCtasNarrow>(a, sh, s, l2win)
+                     : launch_persistent_as<false, kCtasNarrow>(a, sh, s, l2win);
+}
+
 }  // namespace
 
-int sssp_max_ctas_per_sm(int block) {
+int sssp_max_ctas_per_sm(int block, int wide) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_persistent_kernel<true>, block, 0) !=
-      cudaSuccess)
-    return 1;
+  const cudaError_t e =
+      wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &n, sssp_persistent_kernel<true, kCtasWide>, block, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &n, sssp_persistent_kernel<true, kCtasNarrow>, block, 0);
+  if (e != cudaSuccess) return 1;
   return n < 1 ? 1 : n;
 }
 
@@ -534,25 +578,8 @@ cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape r
                         cudaStream_t s, const cudaAccessPolicyWindow* l2win) {
   sssp_init_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a);
   if (ev0) cudaEventRecord(ev0, s);
-  if (l2win) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(run_shape.grid);
-    cfg.blockDim = dim3(run_shape.block);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[0].val.accessPolicyWindow = *l2win;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = a.relax_min ? cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<true>, a)
-                                      : cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<false>, a);
-    if (e != cudaSuccess) return e;
-  } else {
-    if (a.relax_min)
-      sssp_persistent_kernel<true><<<run_shape.grid, run_shape.block, 0, s>>>(a);
-    else
-      sssp_persistent_kernel<false><<<run_shape.grid, run_shape.block, 0, s>>>(a);
-  }
+  const cudaError_t e = launch_persistent(a, run_shape, s, l2win);
+  if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, s);
   sssp_epilogue_kernel<<<init_shape.grid, init_shape.block, 0, s>>>(a, status_dev, nullptr);
   if (a.pred)
@@ -594,11 +621,7 @@ cudaError_t launch_queue_reset(QueueSet qs, cudaStream_t s) {
 
 cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape,
                                         cudaStream_t s) {
-  if (a.relax_min)
-    sssp_persistent_kernel<true><<<run_shape.grid, run_shape.block, 0, s>>>(a);
-  else
-    sssp_persistent_kernel<false><<<run_shape.grid, run_shape.block, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_persistent(a, run_shape, s, nullptr);
 }
 
 cudaError_t launch_sssp_epilogue(const SsspArgs& a, LaunchShape shape, int32_t* status_dev,

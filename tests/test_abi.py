@@ -80,10 +80,12 @@ def test_tune_struct_layout_matches_the_header():
     assert t.cycle_walk_hops == 64 and t.relax_atomic == bfq.RELAX_AUTO
     assert t.neg_cycle_mode == bfq.NEG_CYCLE_STOP and t.batch_budget_klabels == 0
     assert t.share_div == 2 and t.chunk_batch == 4 and t.l2_persist_pct == 0
+    assert t.kernel_ctas == 0
 
 
 @pytest.mark.parametrize("field,value", [("relax_atomic", 3), ("neg_cycle_mode", 2),
-                                         ("cycle_walk_hops", 1), ("l2_persist_pct", 101)])
+                                         ("cycle_walk_hops", 1), ("l2_persist_pct", 101),
+                                         ("kernel_ctas", 2), ("kernel_ctas", 5)])
 def test_bad_tunes_rejected_before_any_device_work(field, value):
     import numpy as np
     h = ctypes.c_void_p()

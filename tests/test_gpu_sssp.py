@@ -128,6 +128,10 @@ def test_rmat22_full_all_sources():
     dict(relax_atomic=1),
     dict(relax_atomic=2),
     dict(relax_atomic=2, hub_degree=32, chunk_edges=32, batch_items=4),
+    dict(kernel_ctas=3),
+    dict(kernel_ctas=4),
+    dict(kernel_ctas=3, relax_atomic=2, hub_degree=32, chunk_edges=32, batch_items=4),
+    dict(kernel_ctas=3, ctas_per_sm=2, queues_per_cta=2),
 ], ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
 def test_tunes(tune):
     g = synth.workload_rmat(14)
@@ -197,6 +201,57 @@ def test_cycle_then_clean_on_one_handle():
             assert ost == (oracle.NEG_CYCLE if src >= V else oracle.OK)
     finally:
         bfq.bfq_graph_destroy(h)
+
+
+def _two_copies_cycle_in_second(side=60):
+    base = synth.grid_graph(side, side, seed=5)
+    V = base.V
+    u = base.tails().astype(np.int64)
+    v = base.col.astype(np.int64)
+    rp, col, order = synth.csr_from_edges(2 * V, np.r_[u, u + V], np.r_[v, v + V],
+                                          return_order=True)
+    two = synth.Graph("two", rp, col, np.r_[base.w, base.w][order].astype(np.int32),
+                      np.array([V], np.int32))
+    return synth.plant_negative_cycle(two, 5, seed=3, reachable_from=[V]), V
+
+
+def test_register_forms_switch_on_one_handle():
+    """The two register forms run different grids over a prefix of the same
+    sub-queues.  Runs that stop on a negative cycle leave queues dirty in one
+    form; the next run, in either form, must reset every sub-queue and be
+    exact; the stats report the grid of the form that ran."""
+    g, V = _two_copies_cycle_in_second()
+    h = gpu_util.create(g)
+    try:
+        grids = {}
+        seq = [(4, V), (3, 0), (3, V + 11), (4, 0), (4, 7), (3, V), (3, 5), (4, V + 3), (4, 9)]
+        for form, src in seq:
+            t = bfq.bfq_graph_get_tune(h)
+            t.kernel_ctas = form
+            bfq.bfq_graph_set_tune(h, t)
+            ost = _compare(g, src, gpu_util.run(h, g.V, src, want_pred=True), check_pred=True)
+            assert ost == (oracle.NEG_CYCLE if src >= V else oracle.OK)
+            st = bfq.bfq_get_stats(h)
+            grids.setdefault(form, set()).add((st["grid"], st["queues"]))
+        assert len(grids[3]) == 1 and len(grids[4]) == 1
+        (g3, q3), = grids[3]
+        (g4, q4), = grids[4]
+        assert g3 <= g4 and q3 <= q4 and g3 * q4 == g4 * q3
+    finally:
+        bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("form", [0, 3, 4])
+def test_register_forms_road_and_hubs(form):
+    t = bfq.make_tune(kernel_ctas=form)
+    for g in (synth.grid_graph(256, 256, seed=8), synth.workload_rmat(13)):
+        h = gpu_util.create(g, t)
+        try:
+            for s in g.sources[:2]:
+                _compare(g, int(s), gpu_util.run(h, g.V, int(s), want_pred=True),
+                         check_pred=True)
+        finally:
+            bfq.bfq_graph_destroy(h)
 
 
 def test_many_runs_reuse_state():
