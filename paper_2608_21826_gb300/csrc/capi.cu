@@ -164,7 +164,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   out->relax_atomic = in->relax_atomic;
   out->kernel_ctas = in->kernel_ctas;
   if (out->threads_per_cta != 256)
-    return invalid("bfq_tune: threads_per_cta must be 256 in this build");
+    return invalid("bfq_tune: threads_per_cta must be 256 (the shared-memory layout of the kernels)");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
     return invalid("bfq_tune: queues_per_cta must be in [1, 8]");
   if (out->batch_items < 1 || out->batch_items > 32)
