@@ -10,6 +10,11 @@ tail is reachable, divided by the summed device time of the queries (CUDA
 events on the launch stream; the graph is resident in HBM; L2 is flushed
 before every query by writing a 256 MiB buffer, outside the timed interval).
 
+The same line carries the other legs as sub-objects (each can be switched
+off with its --no-* flag): batched queries, serving, the standalone queues,
+change-counter rounds, the L2 persistence window, minus-infinity marking and
+the road-like grid in both register forms of the kernel.
+
 --impl reference times the oracle (plain sequential label-correcting
 Bellman-Ford in C) on one host core, one source per step.
 """
