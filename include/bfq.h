@@ -228,11 +228,18 @@ int bfq_get_stats(bfq_graph_t g, bfq_stats* out);
  * Asynchronous on `stream`: returns BFQ_OK once enqueued; the run's status
  * (BFQ_OK, BFQ_NEG_CYCLE, BFQ_RANGE, BFQ_ERR_TIMEOUT, or BFQ_ERR_INVALID if
  * the CSR fails the device-side check) is written to *status_dev.
+ * There is no pred output and no graph handle: the CSR is read in place, and
+ * negative cycles are always reported by stopping (BFQ_NEG_CYCLE_STOP).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call reuses the same array and clears
- * the parts it needs, so calls whose GPU work overlaps (on two streams, or
- * from two threads) race and must be serialised by the caller. */
+ * (cudaGetSymbolAddress) and the device's L2 size with that device current,
+ * and keeps both for the life of the process (a cudaDeviceReset is not
+ * supported afterwards); make that first call before any stream capture.
+ * Every call reuses the same array and clears the parts it needs, so calls
+ * whose GPU work overlaps (on two streams, or from two threads) race and
+ * must be serialised by the caller. */
+int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
+                     int64_t E, int32_t src, int32_t* dist, int32_t* hops,
+                     int32_t* status_dev, void* stream);
 /* ---- round-based Bellman-Ford (Algorithm 3's formulation, Sec. III-C) ---
  * Algorithm 3 relaxes the edge list in synchronous rounds, counts the label
  * decreases of each round in a change counter, stops after a round with no
@@ -281,9 +288,6 @@ int bfq_sssp_rounds(bfq_graph_t g, int32_t src, int32_t flags, int32_t* dist,
 int bfq_graph_get_tune(bfq_graph_t g, bfq_tune* out);
 int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
 
-int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int32_t V,
-                     int64_t E, int32_t src, int32_t* dist, int32_t* hops,
-                     int32_t* status_dev, void* stream);
 
 /* Pick the run-time parameters (share_div, chunk_batch, batch_items, then
  * kernel_ctas) that make the queries from srcs[0..n) (host array) fastest on

@@ -5,8 +5,9 @@ legs of ``bench.py`` may import this package.  The library under
 ``paper_2608_21826_gb300`` never imports it and shares no code with it.
 
 ``sssp_oracle.c`` holds the plain sequential algorithms (FIFO label-correcting
-Bellman-Ford, Dijkstra, Floyd-Warshall, the predecessor-tree invariant, and
-distances with negative cycles resolved to minus infinity).  This
+Bellman-Ford, the same with the parent-graph search for negative cycles,
+Dijkstra, Floyd-Warshall, the predecessor-tree invariant, and distances with
+negative cycles resolved to minus infinity).  This
 module compiles it with gcc on first use (or from ``build()``) and exposes thin
 numpy wrappers.  ``broker_queue.py`` models the Broker Queue of Algorithm 1.
 """
@@ -53,6 +54,8 @@ def _bind(lib):
         f = getattr(lib, name)
         f.argtypes = [i32, p32, p32, p32, i32, p32, p32]
         f.restype = ctypes.c_int
+    lib.oracle_spfa_cycle_search.argtypes = [i32, p32, p32, p32, i32, p32, p32, p64, p32]
+    lib.oracle_spfa_cycle_search.restype = ctypes.c_int
     lib.oracle_spfa_neg_inf.argtypes = [i32, p32, p32, p32, i32, p32, p32]
     lib.oracle_spfa_neg_inf.restype = ctypes.c_int
     lib.oracle_check_pred.argtypes = [i32, p32, p32, p32, i32, p32, p32]
@@ -82,6 +85,9 @@ class Variant:
 
     def dijkstra(self, *a):
         return dijkstra(*a, _lib=self._lib)
+
+    def spfa_cycle_search(self, *a):
+        return spfa_cycle_search(*a, _lib=self._lib)
 
     def spfa_neg_inf(self, *a):
         return spfa_neg_inf(*a, _lib=self._lib)
@@ -117,6 +123,25 @@ def spfa(row_ptr, col, w, src: int, _lib=None):
     if st < 0:
         raise ValueError(f"oracle_spfa rejected its input ({st})")
     return st, dist, hops, scanned.value
+
+
+def spfa_cycle_search(row_ptr, col, w, src: int, _lib=None):
+    """FIFO label-correcting Bellman-Ford with the amortized parent-graph
+    search for negative cycles (exact, and fast on large graphs with a
+    negative cycle).  Returns (status, dist, hops, scanned, cycle_vertex):
+    the labels and scan count equal spfa's when no negative cycle is
+    reachable; cycle_vertex is a vertex on the cycle the search found, or -1."""
+    V, row_ptr, col, w = _csr(row_ptr, col, w)
+    dist = np.empty(V, np.int32)
+    hops = np.empty(V, np.int32)
+    scanned = ctypes.c_int64(0)
+    cv = ctypes.c_int32(-1)
+    st = (_lib or _load()).oracle_spfa_cycle_search(V, _p(row_ptr), _p(col), _p(w), int(src),
+                                                    _p(dist), _p(hops), ctypes.byref(scanned),
+                                                    ctypes.byref(cv))
+    if st < 0:
+        raise ValueError(f"oracle_spfa_cycle_search failed ({st})")
+    return st, dist, hops, scanned.value, cv.value
 
 
 NEG_INF_DIST = -2147483648      # dist of a vertex reachable from a negative cycle

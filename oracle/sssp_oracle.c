@@ -124,6 +124,128 @@ int oracle_spfa(int32_t V, const int32_t* row_ptr, const int32_t* col,
 }
 
 /*
+ * The same FIFO label-correcting Bellman-Ford, with a faster exact test for a
+ * reachable negative cycle: the parent-graph search (Tarjan's observation, in
+ * the "amortized search" form studied by Cherkassky and Goldberg, "Negative-
+ * cycle detection algorithms", Math. Programming 85, 1999).  It is here so
+ * that the status of queries on graphs of a million vertices with a planted
+ * negative cycle can be decided in seconds; oracle_spfa needs about V/|C|
+ * passes around a cycle C before a label reaches V hops.
+ *
+ *   - Every accepted label records its parent p[v] = u and the weight pw[v]
+ *     of the edge (u, v) that produced it.
+ *   - After every V accepted labels, the parent graph (one out-pointer per
+ *     vertex) is searched for a cycle by walking the pointers from every
+ *     vertex, marking each walk with its own number.
+ *   - A cycle of the parent graph has negative weight.  For each parent edge,
+ *     label(v) >= label(p[v]) + (pw[v], 1) holds from the moment it is set
+ *     (later relaxations only lower label(p[v])), strictly for the edge set
+ *     last; summed around the cycle in the ordered group Z^2 (lexicographic
+ *     order) this gives (sum pw, length) < (0, 0), and as length > 0 the
+ *     weight sum is negative.  Its vertices hold labels, so it is reachable.
+ *     The code adds the weights up and checks the sign all the same; a
+ *     non-negative sum would be a bug and returns ORC_ERR_INTERNAL.
+ *   - Conversely, with a reachable negative cycle the labels never settle, so
+ *     either the parent graph closes a cycle or a label reaches V hops (the
+ *     test of oracle_spfa, kept as the fallback), whichever comes first.
+ * Without a reachable negative cycle the parent graph is a tree and nothing
+ * changes: dist, hops, the order of relaxations and *n_relax are those of
+ * oracle_spfa.  *cycle_vertex (nullable) receives a vertex of the cycle found
+ * by the search, or -1 (no cycle, or the hops test fired first).
+ */
+#define ORC_ERR_INTERNAL (-3)
+
+static int64_t parent_graph_cycle(int32_t V, const int32_t* p, int64_t* mark,
+                                  int64_t* walk) {
+  /* returns a vertex on a cycle of the parent graph, or -1 */
+  for (int32_t v = 0; v < V; ++v) mark[v] = 0;
+  for (int32_t v = 0; v < V; ++v) {
+    if (mark[v] != 0) continue;
+    ++*walk;
+    int32_t x = v;
+    while (x >= 0 && mark[x] == 0) {
+      mark[x] = *walk;
+      x = p[x];
+    }
+    if (x >= 0 && mark[x] == *walk) return x;
+  }
+  return -1;
+}
+
+int oracle_spfa_cycle_search(int32_t V, const int32_t* row_ptr, const int32_t* col,
+                             const int32_t* w, int32_t src, int32_t* dist,
+                             int32_t* hops, int64_t* n_relax, int32_t* cycle_vertex) {
+  if (!check_csr(V, row_ptr, col, src)) return ORC_ERR_INVALID;
+  int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  int64_t* h = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  int32_t* fifo = (int32_t*)malloc(sizeof(int32_t) * (size_t)V);
+  char* inq = (char*)calloc((size_t)V, 1);
+  int32_t* p = (int32_t*)malloc(sizeof(int32_t) * (size_t)V);
+  int64_t* pw = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+  if (!d || !h || !fifo || !inq || !p || !pw || !mark) {
+    free(d); free(h); free(fifo); free(inq); free(p); free(pw); free(mark);
+    return ORC_ERR_OOM;
+  }
+  for (int32_t v = 0; v < V; ++v) { d[v] = ORC_INF32; h[v] = -1; p[v] = -1; pw[v] = 0; }
+  d[src] = 0;
+  h[src] = 0;
+  int64_t qhead = 0, qlen = 1;
+  fifo[0] = src;
+  inq[src] = 1;
+  int status = ORC_OK;
+  int64_t scanned = 0, since_search = 0, walk = 0;
+  int32_t found = -1;
+  while (qlen > 0 && status == ORC_OK) {
+    int32_t u = fifo[qhead];
+    qhead = (qhead + 1) % V;
+    --qlen;
+    inq[u] = 0;
+    int64_t du = d[u], hu = h[u];
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+      ++scanned;
+      int32_t v = col[e];
+      int64_t nd = du + (int64_t)w[e];
+      int64_t nh = hu + 1;
+      if (nd >= ORC_INF32) continue;
+      if (!lex_less(nd, nh, d[v], h[v])) continue;
+      if (nd <= ORC_MIN32) { status = ORC_RANGE; break; }
+      d[v] = nd;
+      h[v] = nh;
+      p[v] = u;
+      pw[v] = w[e];
+      if (nh >= V) { status = ORC_NEG_CYCLE; break; }
+      if (!inq[v]) {
+        inq[v] = 1;
+        fifo[(qhead + qlen) % V] = v;
+        ++qlen;
+      }
+      if (++since_search >= V) {
+        since_search = 0;
+        int64_t c = parent_graph_cycle(V, p, mark, &walk);
+        if (c >= 0) {
+          int64_t sum = 0;
+          int32_t x = (int32_t)c;
+          do { sum += pw[x]; x = p[x]; } while (x != (int32_t)c);
+          if (sum >= 0) { status = ORC_ERR_INTERNAL; break; }
+          found = (int32_t)c;
+          status = ORC_NEG_CYCLE;
+          break;
+        }
+      }
+    }
+  }
+  for (int32_t v = 0; v < V; ++v) {
+    dist[v] = (int32_t)(d[v] >= ORC_INF32 ? ORC_INF32 : d[v]);
+    hops[v] = (int32_t)h[v];
+  }
+  if (n_relax) *n_relax = scanned;
+  if (cycle_vertex) *cycle_vertex = found;
+  free(d); free(h); free(fifo); free(inq); free(p); free(pw); free(mark);
+  return status;
+}
+
+/*
  * Distances with negative cycles resolved.  The paper stops at reporting that
  * a negative cycle is reachable; this states the usual refinement of that
  * answer, which the library offers as an option: d(v) = -infinity exactly

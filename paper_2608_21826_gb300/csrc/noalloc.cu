@@ -32,6 +32,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_setup_mu;
 void* g_scratch_dev[kNoAllocMaxDevices] = {};
+long long g_l2_bytes[kNoAllocMaxDevices] = {};
 
 // Byte offsets of the per-call working set inside the scratch array.
 struct Layout {
@@ -101,9 +102,9 @@ __global__ void noalloc_init_kernel(SsspArgs a, const int* bad) {
   }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
-int scratch_for_current_device(unsigned char** out, int* dev_out) {
+// Device address of the scratch array on the current device and the
+// device's L2 size, looked up once per device (with that device current).
+int scratch_for_current_device(unsigned char** out, int* dev_out, long long* l2_out) {
   int dev = 0;
   BFQ_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) {
@@ -114,10 +115,14 @@ int scratch_for_current_device(unsigned char** out, int* dev_out) {
   if (!g_scratch_dev[dev]) {
     void* p = nullptr;
     BFQ_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    int l2 = 0;
+    BFQ_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    g_l2_bytes[dev] = l2;
     g_scratch_dev[dev] = p;
   }
   *out = (unsigned char*)g_scratch_dev[dev];
   *dev_out = dev;
+  *l2_out = g_l2_bytes[dev];
   return BFQ_OK;
 }
 
@@ -156,7 +161,8 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   }
   unsigned char* base = nullptr;
   int dev = 0;
-  int rc = scratch_for_current_device(&base, &dev);
+  long long l2_bytes = 0;
+  int rc = scratch_for_current_device(&base, &dev, &l2_bytes);
   if (rc != BFQ_OK) return rc;
   int sms = 0;
   BFQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -189,7 +195,9 @@ extern "C" int bfq_sssp_noalloc(const int32_t* row_ptr, const int32_t* adj, int3
   a.spin_limit = 1LL << 22;
   a.time_limit_ns = 20000LL * 1000000LL;
   a.phantom = 0;
-  a.relax_min = 1;                 // at most 4 MiB of labels: they stay in L2
+  // one atomicMin per relaxation while the labels fit in half of L2 (the
+  // rule of the regular entry point; always so at the vertex limit on GB300)
+  a.relax_min = (long long)sizeof(long long) * V <= l2_bytes / 2 ? 1 : 0;
   int* bad = (int*)(base + L.bad);
 
   BFQ_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));

@@ -1,6 +1,8 @@
 """Shared test helpers: golden-fixture parsing and small brute-force checks."""
 from __future__ import annotations
 
+import concurrent.futures as cf
+import functools
 import glob
 import itertools
 import os
@@ -177,3 +179,25 @@ def shifted_expectation(dist_base, hops_base, p, s):
     d = dist_base.astype(np.int64)
     out = np.where(d == INF, INF, d + p[s] - p)
     return out, hops_base
+
+
+@functools.lru_cache(maxsize=1)
+def batched_workload():
+    """The full batched mix (64 graphs, 512 queries), generated once per
+    test process."""
+    return synth.workload_batched()
+
+
+def oracle_many(jobs, threads=None):
+    """Run oracle.spfa_cycle_search on many (graph, src) jobs in threads (the
+    oracle is C called through ctypes, which releases the GIL; no processes
+    are forked).  Returns a list of (status, dist, hops) in job order."""
+    import oracle
+
+    def one(job):
+        g, s = job
+        st, d, h, _, _ = oracle.spfa_cycle_search(g.row_ptr, g.col, g.w, int(s))
+        return st, d, h
+
+    with cf.ThreadPoolExecutor(max_workers=threads or min(16, os.cpu_count() or 4)) as ex:
+        return list(ex.map(one, jobs))

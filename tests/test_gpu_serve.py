@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2608_21826_gb300 import bfq, synth
-from tests import gpu_util
+from tests import gpu_util, helpers
 
 pytestmark = pytest.mark.gpu
 
@@ -159,4 +159,53 @@ def test_large_requests_run_alone_between_small_ones():
             assert sst == ost and np.array_equal(sd, od)
     finally:
         for h in all_h:
+            bfq.bfq_graph_destroy(h)
+
+
+def test_full_serving_mix_matches_oracle():
+    """The serving workload at full size: the 64-graph batched mix plus an
+    R-MAT scale-23 graph (8.4M vertices, 131M edges) resident in one server.
+    240 requests over the mix and 4 on R-MAT 23 arrive in Poisson-like
+    trickles, so many are admitted while others run and the large ones run
+    alone between batches.  Every result (status, dist, hops) equals the
+    oracle's, element by element."""
+    import torch
+    graphs, _ = helpers.batched_workload()
+    g23 = synth.workload_rmat(23)
+    all_g = list(graphs) + [g23]
+    rng = np.random.default_rng(2024)
+    reqs = []
+    for k in range(240):
+        gi = int(rng.integers(0, len(graphs)))
+        reqs.append((gi, int(rng.choice(graphs[gi].sources))))
+        if k % 60 == 30:
+            reqs.append((len(graphs), int(g23.sources[(k // 60) % len(g23.sources)])))
+    expect = helpers.oracle_many([(all_g[gi], s) for gi, s in reqs])
+    handles = [gpu_util.create(g) for g in all_g]
+    sv = bfq.bfq_server_create(handles, 32 * 400_000_000, 512)
+    try:
+        bufs = [(torch.full((all_g[gi].V,), -3, dtype=torch.int32, device="cuda"),
+                 torch.full((all_g[gi].V,), -3, dtype=torch.int32, device="cuda"))
+                for gi, _ in reqs]
+        torch.cuda.synchronize()
+        ids = []
+        for k, (gi, s) in enumerate(reqs):
+            ids.append(bfq.bfq_server_submit(sv, gi, s, bufs[k][0], bufs[k][1]))
+            if k % 16 == 15:
+                time.sleep(float(rng.exponential(0.002)))
+        sts = [bfq.bfq_server_wait(sv, rid, 120000) for rid in ids]
+        assert bfq.bfq_server_stats(sv)["completed"] == len(reqs)
+        assert bfq.bfq_server_stats(sv)["peak_active"] > 1
+        n_cyc = 0
+        for k, ((gi, s), st) in enumerate(zip(reqs, sts)):
+            ost, od, oh = expect[k]
+            assert st == ost, (k, gi, s, st, ost)
+            n_cyc += st == bfq.NEG_CYCLE
+            if st == bfq.OK:
+                assert np.array_equal(bufs[k][0].cpu().numpy(), od), (k, gi, s)
+                assert np.array_equal(bufs[k][1].cpu().numpy(), oh), (k, gi, s)
+        assert n_cyc > 0
+    finally:
+        bfq.bfq_server_destroy(sv)
+        for h in handles:
             bfq.bfq_graph_destroy(h)

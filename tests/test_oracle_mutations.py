@@ -95,3 +95,67 @@ def test_mutation_is_caught(tmp_path, name):
     body = body.replace(old, new, 1)
     o = _compile(tmp_path, head + "int oracle_spfa(" + body, name)
     assert _battery(o) is not None, f"pins did not catch mutation {name}"
+
+
+# ---- the parent-graph search of oracle_spfa_cycle_search -------------------
+
+CYCLE_SEARCH_MUTATIONS = {
+    # without parents the search never closes a cycle: only the slow hops test
+    "parent_not_recorded": ("      p[v] = u;\n", "\n"),
+    # a walk that stops on any earlier walk's vertex reports false cycles
+    "walk_id_ignored": ("if (x >= 0 && mark[x] == *walk) return x;",
+                        "if (x >= 0) return x;"),
+    "weight_wrong_sign": ("      pw[v] = w[e];\n", "      pw[v] = -w[e];\n"),
+    "search_never_run": ("if (++since_search >= V) {", "if (++since_search >= 4 * (int64_t)V * V) {"),
+    "dropped_weight": ("      int64_t nd = du + (int64_t)w[e];\n      int64_t nh = hu + 1;\n"
+                       "      if (nd >= ORC_INF32) continue;\n      if (!lex_less",
+                       "      int64_t nd = du;\n      int64_t nh = hu + 1;\n"
+                       "      if (nd >= ORC_INF32) continue;\n      if (!lex_less"),
+}
+
+
+def _battery_cycle(o):
+    """Pins of the cycle search, compact; returns the first failure or None."""
+    try:
+        for seed in range(25):
+            rng = np.random.default_rng(seed)
+            V = int(rng.integers(1, 8))
+            g = synth.random_graph(V, int(rng.integers(0, 3 * V + 1)), seed=1000 + seed,
+                                   wlo=-4, whi=9)
+            neg, bd, bh = helpers.brute_force(g, 0)
+            st, d, h, _, _ = o.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+            if st != (oracle.NEG_CYCLE if neg else oracle.OK):
+                return f"brute force {seed}: status"
+            if not neg and not (np.array_equal(d, bd) and np.array_equal(h, bh)):
+                return f"brute force {seed}: labels"
+        for seed in range(3):
+            g = synth.random_potential_graph(300, 1500, seed=seed)
+            st, d, h, _ = oracle.spfa(g.row_ptr, g.col, g.w, 0)
+            st2, d2, h2, _, _ = o.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+            if st2 != st or not (np.array_equal(d, d2) and np.array_equal(h, h2)):
+                return "agreement with spfa"
+        g = synth.plant_negative_cycle(synth.grid_graph(30, 30, seed=2, src=0), 5, seed=2)
+        st, _, _, n, cv = o.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+        if st != oracle.NEG_CYCLE or n > 20 * g.E or cv not in set(int(x) for x in g.cycle):
+            return "planted cycle found early"
+    except ValueError as e:                 # the routine's own sign check fired
+        return f"internal check: {e}"
+    return None
+
+
+def test_unmutated_cycle_search_passes(tmp_path):
+    assert _battery_cycle(_compile(tmp_path, open(SRC).read(), "clean_cs")) is None
+
+
+@pytest.mark.parametrize("name", sorted(CYCLE_SEARCH_MUTATIONS))
+def test_cycle_search_mutation_is_caught(tmp_path, name):
+    text = open(SRC).read()
+    head, body = text.split("int oracle_spfa_cycle_search(", 1)
+    old, new = CYCLE_SEARCH_MUTATIONS[name]
+    if old not in body:                      # anchors inside the helper above it
+        assert old in head, f"mutation anchor missing: {name}"
+        head = head.replace(old, new, 1)
+    else:
+        body = body.replace(old, new, 1)
+    o = _compile(tmp_path, head + "int oracle_spfa_cycle_search(" + body, name)
+    assert _battery_cycle(o) is not None, f"pins did not catch mutation {name}"

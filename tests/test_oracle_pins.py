@@ -219,3 +219,74 @@ def test_reached_edges_counts_tails():
     st, d, _, _ = oracle.spfa(g.row_ptr, g.col, g.w, 0)
     reach = synth.reachable(g.row_ptr, g.col, 0)
     assert oracle.reached_edges(g.row_ptr, d) == int(np.diff(g.row_ptr)[reach].sum())
+
+
+# ---- spfa_cycle_search: the same FIFO Bellman-Ford with the parent-graph
+# search for negative cycles (used where spfa's hops >= V test is too slow)
+
+@pytest.mark.parametrize("seed", range(60))
+def test_cycle_search_brute_force_tiny(seed):
+    rng = np.random.default_rng(seed)
+    V = int(rng.integers(1, 8))
+    g = synth.random_graph(V, int(rng.integers(0, 3 * V + 1)), seed=1000 + seed, wlo=-4, whi=9)
+    neg, bd, bh = helpers.brute_force(g, 0)
+    st, d, h, _, cv = oracle.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+    assert st == (oracle.NEG_CYCLE if neg else oracle.OK)
+    if not neg:
+        assert np.array_equal(d, bd) and np.array_equal(h, bh) and cv == -1
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_cycle_search_agrees_with_spfa(seed):
+    """Same status as spfa; without a cycle the same labels and the same scan
+    count (the search changes nothing then)."""
+    rng = np.random.default_rng(20_000 + seed)
+    V = int(rng.integers(2, 300))
+    E = int(rng.integers(V, 5 * V))
+    if seed % 2:
+        g = synth.random_graph(V, E, seed=seed, wlo=-3, whi=30)
+    else:
+        g = synth.random_potential_graph(V, E, seed=seed)
+    st, d, h, n = oracle.spfa(g.row_ptr, g.col, g.w, 0)
+    st2, d2, h2, n2, cv = oracle.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+    assert st == st2
+    if st == oracle.OK:
+        assert np.array_equal(d, d2) and np.array_equal(h, h2) and n == n2 and cv == -1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cycle_search_planted_cycles(seed):
+    """A planted 5-cycle reachable from the source is found early, and the
+    vertex reported lies on it; planted where the source cannot reach it, the
+    status is OK with the labels of the graph without it."""
+    base = synth.grid_graph(60, 60, seed=seed, wmax=100, pmax=50, src=0)
+    g = synth.plant_negative_cycle(base, 5, seed=seed)
+    st, _, _, n, cv = oracle.spfa_cycle_search(g.row_ptr, g.col, g.w, 0)
+    assert st == oracle.NEG_CYCLE
+    assert cv in set(int(x) for x in g.cycle)
+    assert n <= 20 * g.E                # spfa's hops test needs about V/5 laps
+    # the same kind of cycle in a second, unreachable copy of the grid
+    V = base.V
+    u = base.tails().astype(np.int64)
+    v = base.col.astype(np.int64)
+    rp, col, order = synth.csr_from_edges(2 * V, np.r_[u, u + V], np.r_[v, v + V],
+                                          return_order=True)
+    two = synth.Graph("two", rp, col, np.r_[base.w, base.w][order].astype(np.int32),
+                      np.array([0], np.int32),
+                      base_w=np.r_[base.base_w, base.base_w][order],
+                      potential=np.r_[base.potential, base.potential])
+    far = synth.plant_negative_cycle(two, 5, seed=seed, reachable_from=[])
+    assert np.all(far.cycle >= V)
+    st, d, h, _, cv = oracle.spfa_cycle_search(far.row_ptr, far.col, far.w, 0)
+    st0, d0, h0, _ = oracle.spfa(far.row_ptr, far.col, far.w, 0)
+    assert st == st0 == oracle.OK and cv == -1
+    assert np.array_equal(d, d0) and np.array_equal(h, h0)
+
+
+def test_cycle_search_cycle_through_source_and_golden():
+    for path in helpers.golden_files():
+        g, exp = helpers.load_golden(path)
+        st, d, h, _, _ = oracle.spfa_cycle_search(g.row_ptr, g.col, g.w, int(g.sources[0]))
+        assert st == exp["status"], path
+        if "dist" in exp:
+            assert d.tolist() == exp["dist"] and h.tolist() == exp["hops"], path
