@@ -11,9 +11,12 @@ events on the launch stream; the graph is resident in HBM; L2 is flushed
 before every query by writing a 256 MiB buffer, outside the timed interval).
 
 The same line carries the other legs as sub-objects (each can be switched
-off with its --no-* flag): batched queries, serving, the standalone queues,
-change-counter rounds, the L2 persistence window, minus-infinity marking and
-the road-like grid in both register forms of the kernel.
+off with its --no-* flag): batched queries (with their roofline), serving,
+the standalone queues, the two worklist reservation forms, change-counter
+rounds, the L2 persistence window, minus-infinity marking, and the road-like
+1M grid and the 64x64 grid (each autotuned, with GTEPS, roofline and rounds).
+Headline scalars of the batched and serving legs are repeated at the top
+level.
 
 --impl reference times the oracle (plain sequential label-correcting
 Bellman-Ford in C) on one host core, one source per step.
@@ -57,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--no-l2", action="store_true")
     p.add_argument("--no-neg-inf", action="store_true")
     p.add_argument("--no-road", action="store_true")
+    p.add_argument("--no-grid", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default run-time parameters (profiling runs)")
     p.add_argument("--serve-requests", type=int, default=2000,
@@ -169,13 +174,17 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the persistent kernel's code (comments and blank lines left
-    out, so a comment edit does not invalidate the committed counters)."""
+SSSP_SOURCES = ("sssp.cu", "sssp_common.cuh", "bfq_device.cuh", "bfq_internal.h")
+BATCH_TRAFFIC = os.path.join(ROOT, "profiles", "batch_persistent_batched64_traffic.txt")
+
+
+def kernel_source_hash(names=SSSP_SOURCES):
+    """Hash of a kernel's code (comments and blank lines left out, so a
+    comment edit does not invalidate the committed counters)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("sssp.cu", "sssp_common.cuh", "bfq_device.cuh", "bfq_internal.h"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2608_21826_gb300", "csrc", name)) as f:
             src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -185,17 +194,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
+def profiled_traffic(workload, path=PROFILE_TRAFFIC, names=SSSP_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
     try:
         kv = {}
-        with open(PROFILE_TRAFFIC) as f:
+        with open(path) as f:
             for ln in f:
                 if "=" in ln and not ln.startswith("#"):
                     k, v = ln.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_hash") != kernel_source_hash():
+        if kv.get("kernel_source_hash") != kernel_source_hash(names):
             return None
         if kv.get("workload") != workload:
             return None
@@ -238,10 +247,13 @@ def batched_leg(dev, reps=5, autotune=True):
         bfq.bfq_batch_set_tune(b, tune)
     for _ in range(2):
         bfq.bfq_sssp_batch(b, queries[:, 0], queries[:, 1], dist)
-    ms = []
+    ms, deq, rel = [], 0, 0
     for _ in range(reps):
         rc, st = bfq.bfq_sssp_batch(b, queries[:, 0], queries[:, 1], dist)
-        ms.append(bfq.bfq_batch_get_stats(b)["kernel_ms"])
+        bst = bfq.bfq_batch_get_stats(b)
+        ms.append(bst["kernel_ms"])
+        deq += bst["dequeued"]
+        rel += bst["relaxed"]
     n_cyc = int(np.sum(st == bfq.NEG_CYCLE))
     n_ok = int(np.sum(st == bfq.OK))
     # m_reached per query (untimed solo pass with stats), then plain timing
@@ -265,12 +277,25 @@ def batched_leg(dev, reps=5, autotune=True):
             plain_ms.append(e0.elapsed_time(e1))
     t_b = float(np.median(ms))
     t_p = float(np.median(plain_ms))
+    # algorithmic bytes of one launch, as for the single query: 4 B per
+    # vertex of every query (init) + 20 B per dequeued item + 12 B per edge
+    b_eff = 4.0 * total + (20.0 * deq + 12.0 * rel) / reps
+    peak, _ = measured_peak_hbm()
     out = {"workload": "batched64: 64 graphs, 512 queries (6 graphs with planted cycles)",
            "queries": nq, "graphs": len(graphs), "total_vertices": total,
            "total_edges": int(sum(g.E for g in graphs)),
            "ms_per_batch": t_b, "qps": nq / (t_b / 1e3),
            "plain_ms": t_p, "plain_qps": nq / (t_p / 1e3), "speedup_vs_plain": t_p / t_b,
            "gteps": m_reached / (t_b / 1e3) / 1e9, "neg_cycle_queries": n_cyc, "ok_queries": n_ok,
+           "roofline": {"bound": "hbm", "algorithmic_bytes_per_launch": b_eff,
+                        "achieved": b_eff / (t_b / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": b_eff / (t_b / 1e3) / 1e9 / peak,
+                        "traffic": profiled_traffic("batched64", BATCH_TRAFFIC,
+                                                    ("batch.cu", "sssp_multi.cuh",
+                                                     "sssp_common.cuh", "bfq_device.cuh",
+                                                     "bfq_internal.h")),
+                        "work_ratio": rel / reps / max(1.0, m_reached),
+                        "kernel": "batch_persistent_kernel (whole captured launch timed)"},
            "tune": {"share_div": tune.share_div, "chunk_batch": tune.chunk_batch,
                     "batch_items": tune.batch_items},
            "timing": "CUDA events around the captured graph launch (batch) and around the "
@@ -403,7 +428,8 @@ def queue_leg(dev, n_ops=10_000_000):
     out = torch.empty(n_ops, dtype=torch.int32, device=dev)
     shapes = [(108, 256), (216, 512), (152 * 8, 256)]
     res = {}
-    for name, var in (("bq", bfq.QUEUE_BQ), ("bwd", bfq.QUEUE_BWD), ("bq_warp", bfq.QUEUE_BQ_WARP)):
+    for name, var in (("bq", bfq.QUEUE_BQ), ("bwd", bfq.QUEUE_BWD), ("bq_warp", bfq.QUEUE_BQ_WARP),
+                      ("bwd_warp", bfq.QUEUE_BWD_WARP)):
         q = bfq.bfq_queue_create(n_ops, var)
         best = {}
         try:
@@ -449,11 +475,17 @@ def queue_leg(dev, n_ops=10_000_000):
                 frac[name] = res[name]["enqdeq"]["ops_per_s"] / peaks["same_address_ticket_add"]
     if peaks["same_address_warp_cas"] > 0 and "enqdeq" in res.get("bq_warp", {}):
         frac["bq_warp"] = res["bq_warp"]["enqdeq"]["ops_per_s"] / peaks["same_address_warp_cas"]
+    if peaks["same_address_ticket_add"] > 0 and "enqdeq" in res.get("bwd_warp", {}):
+        # two one-address atomics (reservation, ticket) per 32 operations
+        frac["bwd_warp"] = (res["bwd_warp"]["enqdeq"]["ops_per_s"] /
+                            (16.0 * peaks["same_address_ticket_add"]))
     return {"ops": n_ops, "variants": res, "atomic_peaks_ops_per_s": peaks,
             "enqdeq_frac_of_atomic_peak": frac,
             "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts; "
-                    "per-thread BQ/BWD against one-address ticket adds, the warp-aggregated "
-                    "queue against one-address warp compare-and-swap"}
+                    "per-thread BQ/BWD against one-address ticket adds, the exact-count "
+                    "warp queue against one-address warp compare-and-swap, the single-shot "
+                    "warp queue against 16 x one-address ticket adds (two atomics per "
+                    "32 operations)"}
 
 
 def rounds_leg(h, srcs, dist_t, flush, stream, m_per_query, queue_kernel_ms):
@@ -556,49 +588,126 @@ def neg_inf_leg(g, dev, reps=3):
     return out
 
 
-def road_leg(dev, reps=3):
-    """The road-like 1024^2 grid (low out-degree): device time per query of
-    the persistent kernel in each register form and as autotuned, exact
-    against the oracle on the first source."""
+def small_graph_leg(dev, g, name, reps=3, rounds=True):
+    """One of the smaller configurations on its own handle: device time per
+    query of the persistent kernel in each register form and as autotuned,
+    GTEPS, the algorithmic-bytes roofline of the autotuned form, the
+    change-counter rounds on the same sources, and exactness against the
+    oracle on the first source.  L2 is flushed before every query."""
     import torch
     import oracle
-    from paper_2608_21826_gb300 import bfq, synth
-    g = synth.workload_road1m()
+    from paper_2608_21826_gb300 import bfq
     srcs = [int(x) for x in g.sources]
     h = bfq.bfq_graph_create(g.row_ptr, g.col, g.w)
     dist = torch.empty(g.V, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = {"workload": "road1m: 1024^2 grid, 10% edges dropped, 1% shortcuts, 8 sources",
-           "V": g.V, "E": g.E}
+    stream = torch.cuda.current_stream(dev)
+    peak, _ = measured_peak_hbm()
+    out = {"workload": name, "V": g.V, "E": g.E, "sources": len(srcs)}
 
-    def per_query_ms():
-        ks = []
+    def per_query():
+        ks, calls, deq, rel, m = [], [], 0, 0, 0
         for r in range(reps + 1):
             for s in srcs:
                 flush.fill_(r & 0xFF)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
                 st = bfq.bfq_sssp(h, s, dist)
+                t1 = time.perf_counter()
                 if st != bfq.OK:
-                    raise SystemExit(f"bench road: status {st}")
+                    raise SystemExit(f"bench {name}: status {st}")
                 if r > 0:
-                    ks.append(bfq.bfq_get_stats(h)["kernel_ms"])
-        return sum(ks) / len(ks)
+                    x = bfq.bfq_get_stats(h)
+                    ks.append(x["kernel_ms"])
+                    calls.append((t1 - t0) * 1e3)
+                    deq += x["dequeued"]
+                    rel += x["relaxed"]
+                    m += x["m_reached"]
+        n = len(ks)
+        k = sum(ks) / n
+        b_eff = 4.0 * g.V + (20.0 * deq + 12.0 * rel) / n
+        return {"kernel_ms_per_query": k, "call_ms_per_query": sum(calls) / n,
+                "gteps": m / n / (k / 1e3) / 1e9, "work_ratio": rel / max(1, m),
+                "m_reached_per_query": m / n,
+                "roofline": {"bound": "hbm", "algorithmic_bytes_per_launch": b_eff,
+                             "achieved": b_eff / (k / 1e3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": b_eff / (k / 1e3) / 1e9 / peak}}
 
     try:
         for form in (4, 3):
             t = bfq.bfq_graph_get_tune(h)
             t.kernel_ctas = form
             bfq.bfq_graph_set_tune(h, t)
-            out[f"kernel_ms_per_query_ctas{form}"] = per_query_ms()
+            out[f"kernel_ms_per_query_ctas{form}"] = per_query()["kernel_ms_per_query"]
         t = bfq.bfq_autotune(h, srcs)
-        out["autotuned"] = {"share_div": t.share_div, "chunk_batch": t.chunk_batch,
-                            "batch_items": t.batch_items, "kernel_ctas": t.kernel_ctas,
-                            "kernel_ms_per_query": per_query_ms()}
+        out["tune"] = {"share_div": t.share_div, "chunk_batch": t.chunk_batch,
+                       "batch_items": t.batch_items, "kernel_ctas": t.kernel_ctas,
+                       "queue_form": t.queue_form, "l2_persist_pct": t.l2_persist_pct}
+        out["autotuned"] = per_query()
+        if rounds:
+            try:
+                out["rounds"] = rounds_leg(h, srcs, dist, flush, stream,
+                                           out["autotuned"]["m_reached_per_query"],
+                                           out["autotuned"]["kernel_ms_per_query"])
+            except Exception as e:                           # reported, not fatal
+                out["rounds"] = {"error": repr(e)}
         bfq.bfq_sssp(h, srcs[0], dist)
         ost, od, _, _ = oracle.spfa(g.row_ptr, g.col, g.w, srcs[0])
         out["exact_first_source"] = bool(ost == oracle.OK and
                                          np.array_equal(dist.cpu().numpy(), od))
     finally:
         bfq.bfq_graph_destroy(h)
+    return out
+
+
+def road_leg(dev, reps=3):
+    """The road-like 1024^2 grid (1M vertices, low out-degree, deep)."""
+    from paper_2608_21826_gb300 import synth
+    return small_graph_leg(dev, synth.workload_road1m(),
+                           "road1m: 1024^2 grid, 10% edges dropped, 1% shortcuts, 8 sources",
+                           reps)
+
+
+def grid_leg(dev, reps=5):
+    """The 64x64 grid (4,096 vertices): latency-bound, so the call time of a
+    host-synchronous query is reported beside the kernel time."""
+    from paper_2608_21826_gb300 import synth
+    return small_graph_leg(dev, synth.workload_grid4k(),
+                           "grid4k: 64x64 grid, w U[1,100] + potentials U[0,50], source 0",
+                           reps)
+
+
+def worklist_forms_leg(h, srcs, dist_t, flush, stream, reps=3):
+    """The two reservation forms of the worklist's sub-queues on the same
+    handle and sources, at the handle's other tuned parameters: exact-count
+    (Broker Queue) against single-shot (Broker Work Distributor)."""
+    from paper_2608_21826_gb300 import bfq
+    base = bfq.bfq_graph_get_tune(h)
+    out = {}
+    try:
+        for name, form in (("exact", bfq.QUEUE_FORM_EXACT),
+                           ("single_shot", bfq.QUEUE_FORM_SINGLE_SHOT)):
+            t = bfq.bfq_graph_get_tune(h)
+            t.queue_form = form
+            bfq.bfq_graph_set_tune(h, t)
+            bfq.bfq_sssp(h, srcs[0], dist_t)
+            ks, rel, m = [], 0, 0
+            for r in range(reps):
+                for s in srcs:
+                    flush.fill_(r & 0xFF)
+                    if bfq.bfq_sssp(h, s, dist_t) != bfq.OK:
+                        raise RuntimeError("worklist forms: a query did not finish cleanly")
+                    x = bfq.bfq_get_stats(h)
+                    ks.append(x["kernel_ms"])
+                    rel += x["relaxed"]
+                    m += x["m_reached"]
+            k = sum(ks) / len(ks)
+            out[name] = {"kernel_ms_per_query": k, "work_ratio": rel / max(1, m),
+                         "gteps": m / len(ks) / (k / 1e3) / 1e9}
+    finally:
+        bfq.bfq_graph_set_tune(h, base)
+    out["single_shot_speedup"] = out["exact"]["kernel_ms_per_query"] / \
+        out["single_shot"]["kernel_ms_per_query"]
     return out
 
 
@@ -658,7 +767,9 @@ def run_ours(args):
     tuned = bfq.bfq_graph_get_tune(h) if args.no_autotune else bfq.bfq_autotune(h, srcs)
     tune_desc = {"share_div": tuned.share_div, "chunk_batch": tuned.chunk_batch,
                  "batch_items": tuned.batch_items,
-                 "kernel_ctas": tuned.kernel_ctas or ("3 (auto)" if g.E < 8 * V else "4 (auto)")}
+                 "kernel_ctas": tuned.kernel_ctas or ("3 (auto)" if g.E < 8 * V else "4 (auto)"),
+                 "queue_form": {0: "exact (auto)", 1: "exact", 2: "single_shot"}[tuned.queue_form],
+                 "l2_persist_pct": tuned.l2_persist_pct}
 
     def one_step(record):
         """4 queries; returns per-query (device ms, stats)."""
@@ -730,7 +841,12 @@ def run_ours(args):
     # clocks seen over both timed regions (device-timed and end to end)
     clk = clocks.stop()
 
-    rounds = l2 = None
+    rounds = l2 = forms = None
+    if rank == 0 and not args.no_forms:
+        try:
+            forms = worklist_forms_leg(h, srcs, dist_t, flush, stream)
+        except Exception as e:                               # reported, not fatal
+            forms = {"error": repr(e)}
     if rank == 0 and not args.no_rounds:
         try:
             rounds = rounds_leg(h, srcs, dist_t, flush, stream, m_reached / n_q,
@@ -749,12 +865,17 @@ def run_ours(args):
             neg_inf = neg_inf_leg(g, dev)
         except Exception as e:
             neg_inf = {"error": repr(e)}
-    road = None
+    road = grid = None
     if rank == 0 and not args.no_road:
         try:
             road = road_leg(dev)
         except Exception as e:
             road = {"error": repr(e)}
+    if rank == 0 and not args.no_grid:
+        try:
+            grid = grid_leg(dev)
+        except Exception as e:
+            grid = {"error": repr(e)}
     if rank != 0:
         return
     batched = serve = None
@@ -798,13 +919,23 @@ def run_ours(args):
                      "kernel_ms_per_launch": sum(k_ms) / n_q},
         "work": {"dequeued_per_query": deq / n_q, "relaxed_per_query": rel / n_q,
                  "m_reached_per_query": m_reached / n_q, "work_ratio": rel / max(1, m_reached),
-                 "work_gteps": rel / t_dev / 1e9},
+                 "work_gteps": rel / t_dev / 1e9,
+                 # the same roofline counting each reached edge once (no
+                 # re-relaxation): the useful share of the bytes moved
+                 "useful_frac": (4.0 * V * n_q + 20.0 * deq + 12.0 * m_reached) / k_s / 1e9 / peak},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 3 * n_q,
         "clocks": clk,
+        "batched_speedup_vs_plain": (batched or {}).get("speedup_vs_plain"),
+        "batched_frac": ((batched or {}).get("roofline") or {}).get("frac"),
+        "serve_min_ratio_vs_plain": _serve_min_ratio(serve),
+        "serve_p99_ms_at_half_load": _serve_at(serve, 0.5, "p99_ms"),
+        "serve_p50_ms_at_half_load": _serve_at(serve, 0.5, "p50_ms"),
         "batched": batched,
         "serve": serve,
+        "worklist_forms": forms,
+        "grid": grid,
         "queue": queue,
         "rounds": rounds,
         "l2_window": l2,
@@ -812,6 +943,26 @@ def run_ours(args):
         "road": road,
     }
     print(json.dumps(line), flush=True)
+
+
+def _serve_min_ratio(serve):
+    """Least served/plain throughput ratio over the arrival rates >= 0.5x."""
+    try:
+        r = [x["served_qps"] / x["plain_qps"] for x in serve["rates"]
+             if x["fraction_of_batched_saturation"] >= 0.5]
+        return min(r) if r else None
+    except Exception:
+        return None
+
+
+def _serve_at(serve, frac, key):
+    try:
+        for x in serve["rates"]:
+            if x["fraction_of_batched_saturation"] == frac:
+                return x[key]
+    except Exception:
+        pass
+    return None
 
 
 def main():

@@ -69,8 +69,13 @@ enum {
 enum {
   BFQ_QUEUE_BQ = 0,      /* Broker Queue, one operation per thread (Alg. 1)  */
   BFQ_QUEUE_BWD = 1,     /* Broker Work Distributor: ensure tried once        */
-  BFQ_QUEUE_BQ_WARP = 2  /* Broker Queue, warp-aggregated: one count/ticket
-                            reservation per warp, the form the SSSP path uses */
+  BFQ_QUEUE_BQ_WARP = 2, /* Broker Queue, warp-aggregated: one exact-count
+                            reservation (compare-and-swap) and one ticket
+                            range per warp; the SSSP worklist's default form */
+  BFQ_QUEUE_BWD_WARP = 3 /* Broker Work Distributor, warp-aggregated: one
+                            single-shot fetch-add reservation (no retry) on
+                            one of two counters, then one ticket range; the
+                            SSSP worklist's BFQ_QUEUE_FORM_SINGLE_SHOT     */
 };
 
 typedef struct bfq_graph* bfq_graph_t;
@@ -131,6 +136,13 @@ typedef struct bfq_tune {
                                grid, never above ctas_per_sm).  0 = auto: 3
                                when E < 8 V, else 4.  Results are the same
                                either way; bfq_autotune tries both.         */
+  int32_t queue_form;       /* reservations on bfq_sssp's sub-queues:
+                               BFQ_QUEUE_FORM_AUTO, BFQ_QUEUE_FORM_EXACT (the
+                               Broker Queue's exact count, moved by
+                               compare-and-swap) or BFQ_QUEUE_FORM_SINGLE_SHOT
+                               (the Broker Work Distributor's ensure-once: one
+                               fetch-add on one of two counters, no retry).
+                               Results are the same either way.             */
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
@@ -146,6 +158,12 @@ typedef struct bfq_tune {
  * round-based and allocation-free entry points always STOP. */
 #define BFQ_NEG_CYCLE_STOP 0
 #define BFQ_NEG_CYCLE_MARK 1
+
+/* bfq_tune.queue_form (Sec. III-A: BQ retries its ensure step until the
+ * count is final, BWD tries it once).  AUTO is EXACT. */
+#define BFQ_QUEUE_FORM_AUTO 0
+#define BFQ_QUEUE_FORM_EXACT 1
+#define BFQ_QUEUE_FORM_SINGLE_SHOT 2
 
 /* bfq_tune.relax_atomic */
 #define BFQ_RELAX_AUTO 0
@@ -290,13 +308,14 @@ int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
 
 
 /* Pick the run-time parameters (share_div, chunk_batch, batch_items, then
- * kernel_ctas) that make the queries from srcs[0..n) (host array) fastest on
- * g, keep them on the handle and copy them to *out (nullable).  Times a fixed
- * grid of candidates in the handle's register form over one pass of the
- * sources each, the best four again over four passes, then the other form
- * at the best of them (CUDA events, each pass after an untimed one);
- * allocates one int32[V] scratch array for the duration.  Synchronises
- * `stream`. */
+ * kernel_ctas, queue_form and l2_persist_pct) that make the queries from
+ * srcs[0..n) (host array) fastest on g, keep them on the handle and copy them
+ * to *out (nullable).  Times a fixed grid of candidates in the handle's
+ * register form over one pass of the sources each, the best four again over
+ * four passes, then, one at a time at the best so far, the other register
+ * form, the other queue form and an L2 set-aside of 50 and 75 percent for
+ * the labels (CUDA events, each pass after an untimed one); allocates one
+ * int32[V] scratch array for the duration.  Synchronises `stream`. */
 int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
 
 /* ---- batched queries: many sources over many resident graphs in one

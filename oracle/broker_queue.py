@@ -28,6 +28,11 @@ Two things live here, both written from Sec. III-A and Algorithm 1:
     ``bwd=True`` gives the Broker Work Distributor variant: the ensure step is
     tried once and its failure is final (Sec. III-A, last paragraph).
 
+``WarpQueueSim``
+    The warp-aggregated forms the GPU worklist uses (exact-count and
+    single-shot split counters) as step generators, for the same seeded
+    interleavings.
+
 ``check_fifo_positions``
     The property the GPU queue kernels are checked against: an item dequeued
     at ticket position p is exactly the item enqueued at position p, positions
@@ -166,6 +171,125 @@ class BrokerQueueSim:
         log = []
         item = yield from self._read_data(log)
         return OK, (item, log[0])
+
+
+class WarpQueueSim:
+    """Warp-aggregated forms of the Broker Queue (one reservation and one
+    ticket range for up to 32 items), the forms the GPU worklist uses; the
+    same ring, slot tickets and head/tail as BrokerQueueSim.
+
+    ``form="exact"``: one broker count moved by compare-and-swap to an exact
+    value (retried while the count changes under it), then the ticket range.
+    Every ticket wait is then on an operation already granted.
+
+    ``form="split"``: single-shot reservations (the BWD idea of Sec. III-A,
+    warp-aggregated): two counters, ``free`` (places an enqueuer may take,
+    initially N) and ``avail`` (items a dequeuer may take).  An enqueuer
+    fetch-subtracts k from free, keeps min(max(old, 0), k) and adds the
+    surplus back; takes its tail tickets; publishes the items; then adds its
+    grant to avail.  A dequeuer does the same on avail, takes head tickets, reads and
+    releases the slots, then adds its grant to free.  A transient surplus
+    only understates a counter, and each counter is read by one side only,
+    so no grant exceeds what the other side has already provided; no retry.
+
+    ``form="naive"``: one count moved by fetch-add with the surplus added
+    back -- kept to show that it can strand a waiter (a dequeuer granted an
+    item that the enqueuer then withdraws)."""
+
+    def __init__(self, capacity: int, form: str = "exact"):
+        assert form in ("exact", "split", "naive")
+        self.N = capacity
+        self.form = form
+        self.head = 0
+        self.tail = 0
+        self.count = 0          # exact / naive
+        self.free = capacity    # split
+        self.avail = 0          # split
+        self.tickets = [0] * capacity
+        self.ring = [0] * capacity
+
+    def _fetch_add(self, field: str, v: int) -> int:
+        old = getattr(self, field)
+        setattr(self, field, old + v)
+        return old
+
+    def _reserve(self, k: int, deq: bool):
+        """Returns how many of k operations were granted."""
+        if self.form == "exact":
+            c = self.count
+            yield "step"
+            while True:
+                room = c if deq else self.N - c
+                if room <= 0:
+                    return 0
+                take = min(room, k)
+                nc = c - take if deq else c + take
+                if self.count == c:              # compare-and-swap
+                    self.count = nc
+                    yield "step"
+                    return take
+                c = self.count
+                yield "step"
+        if self.form == "naive":
+            old = self._fetch_add("count", -k if deq else k)
+            yield "step"
+            got = min(max(old, 0), k) if deq else min(max(self.N - old, 0), k)
+            if got < k:
+                self._fetch_add("count", (k - got) if deq else -(k - got))
+                yield "step"
+            return got
+        field = "avail" if deq else "free"
+        old = self._fetch_add(field, -k)
+        yield "step"
+        got = min(max(old, 0), k)
+        if got < k:
+            self._fetch_add(field, k - got)
+            yield "step"
+        return got
+
+    def enqueue_warp(self, items):
+        """Generator: enqueue up to len(items) items at once; returns the
+        list of (item, pos) placed (the first ones)."""
+        got = yield from self._reserve(len(items), deq=False)
+        if got == 0:
+            return []
+        pos = self._fetch_add("tail", got)
+        yield "step"
+        placed = []
+        for i in range(got):
+            p = pos + i
+            slot, lap = p % self.N, p // self.N
+            while self.tickets[slot] != 2 * lap:
+                yield "wait"
+            self.ring[slot] = items[i]
+            self.tickets[slot] = 2 * lap + 1
+            yield "step"
+            placed.append((items[i], p))
+        if self.form == "split":
+            self._fetch_add("avail", got)          # published: dequeuers may take them
+            yield "step"
+        return placed
+
+    def dequeue_warp(self, k: int):
+        """Generator: dequeue up to k items at once; returns [(item, pos)]."""
+        got = yield from self._reserve(k, deq=True)
+        if got == 0:
+            return []
+        pos = self._fetch_add("head", got)
+        yield "step"
+        out = []
+        for i in range(got):
+            p = pos + i
+            slot, lap = p % self.N, p // self.N
+            while self.tickets[slot] != 2 * lap + 1:
+                yield "wait"
+            out.append((self.ring[slot], p))
+            self.tickets[slot] = 2 * (lap + 1)
+            yield "step"
+        if self.form == "split":
+            self._fetch_add("free", got)
+            yield "step"
+        return out
 
 
 def run_interleaved(q: BrokerQueueSim, ops, seed: int, max_steps: int = 2_000_000):

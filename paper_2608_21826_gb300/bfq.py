@@ -18,7 +18,8 @@ from . import _build
 
 OK, NEG_CYCLE, FULL, EMPTY, RANGE, PENDING = 0, 1, 2, 3, 4, 5
 ERR_INVALID, ERR_OOM, ERR_TIMEOUT, ERR_CUDA, ERR_BUDGET = -1, -2, -3, -4, -5
-QUEUE_BQ, QUEUE_BWD, QUEUE_BQ_WARP = 0, 1, 2
+QUEUE_BQ, QUEUE_BWD, QUEUE_BQ_WARP, QUEUE_BWD_WARP = 0, 1, 2, 3
+QUEUE_FORM_AUTO, QUEUE_FORM_EXACT, QUEUE_FORM_SINGLE_SHOT = 0, 1, 2
 INF32 = 2147483647
 
 
@@ -37,7 +38,7 @@ class Tune(ctypes.Structure):
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
                 ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
                 ("relax_atomic", ctypes.c_int32), ("batch_budget_klabels", ctypes.c_int32),
-                ("kernel_ctas", ctypes.c_int32)]
+                ("kernel_ctas", ctypes.c_int32), ("queue_form", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

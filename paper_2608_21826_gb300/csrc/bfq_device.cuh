@@ -14,11 +14,14 @@
 //     the next lap's enqueuer waits for.
 //   - head/tail are 64-bit and never wrap, so "Full" is tail-head >= N and
 //     "Empty" is tail-head <= 0.
-// Warp-aggregated form: a warp reserves k items at once, so the broker count
-// is moved with compare-and-swap to an exact value instead of the paper's
-// add-then-undo.  With an exact count every ticket wait is on an operation
+// Warp-aggregated forms: a warp reserves k items at once.  Exact-count form:
+// the broker count is moved with compare-and-swap to an exact value instead
+// of the paper's add-then-undo; every ticket wait is then on an operation
 // that has already been granted (see the proof sketch at wq_reserve), so no
 // waiter can be stranded by a reservation that is later withdrawn.
+// Single-shot form (BWD's ensure-once): one fetch-add on one of two
+// counters, each read by one side only, so a withdrawn surplus is never
+// visible to the other side (also at wq_reserve).
 #pragma once
 
 #include <cstdint>
@@ -138,24 +141,31 @@ __device__ __forceinline__ long long label_key(long long l) { return l & ~kQueue
 // ---------------------------------------------------------------------------
 // One sub-queue's counters, each in its own 32-byte L2 sector.
 struct alignas(128) QueueMeta {
-  int count;                    // broker count: items granted, not yet taken
+  int count;                    // exact form: broker count, items granted and
+                                //   not yet taken; single-shot form: items
+                                //   published and not yet granted to dequeuers
   int pad0[7];
   unsigned long long head;      // dequeue ticket counter
   unsigned long long pad1[3];
   unsigned long long tail;      // enqueue ticket counter
   unsigned long long pad2[3];
-  unsigned long long pad3[4];
+  int used;                     // single-shot form: places granted to
+                                //   enqueuers and not yet released by dequeuers
+  int pad3[7];
 };
 static_assert(sizeof(QueueMeta) == 128, "QueueMeta layout");
 
 // Slot word: (ticket << 32) | item.  Ticket 2*lap means "free for the
 // enqueuer of lap `lap`", 2*lap+1 "holds the item of lap `lap`"; packing the
 // ticket with the item publishes both with one 8-byte store.
+// split: 0 = exact-count reservations (compare-and-swap on count), 1 =
+// single-shot reservations on two counters (see wq_reserve).
 struct QueueSet {
   QueueMeta* meta;              // [Q]
   unsigned long long* slots;    // [Q << cap_log2]
   int Q;
   int cap_log2;
+  int split;
 };
 
 // Leader-lane reservation on the broker count of one sub-queue.
@@ -171,21 +181,57 @@ struct QueueSet {
 // had E - D <= cap when it took the ticket, so ticket p - cap's dequeue was
 // granted and will free the slot.  Every wait is on an earlier ticket that is
 // already granted, hence no cycle of waits.
+//
+// Single-shot form (split = 1; the Broker Work Distributor's "ensure once"
+// of Sec. III-A, warp-aggregated): two counters, each read by one side only.
+// A dequeuer fetch-subtracts `want` from count (published items), keeps
+// min(max(old, 0), want) and adds the surplus back; an enqueuer does the same
+// on used (granted places) against cap.  One atomic and no retry: a
+// transient surplus only understates what the other warps of the same side
+// see (they take less, or move on), never what the opposite side sees.  The
+// enqueuer adds its grant to count after publishing (wq_after_put) and the
+// dequeuer releases its places from used after freeing the slots
+// (wq_after_take).  Finite waits, by induction on tickets: grants never
+// exceed the counter's true value, so at all times (dequeues granted) <=
+// (items published) <= (tail tickets taken) and (enqueues granted) <= cap +
+// (places released) <= cap + (head tickets taken).  A dequeuer's head ticket
+// p therefore has its tail ticket taken, by an enqueuer whose own wait is on
+// ticket p - cap < p; an enqueuer's tail ticket p >= cap has head ticket
+// p - cap taken, by a dequeuer whose wait is on the item of that earlier
+// ticket, after which it frees the slot.
 __device__ __forceinline__ int wq_reserve(QueueMeta* m, int want, bool is_deq, int cap,
-                                          unsigned long long* pos, int c_hint = -1) {
+                                          unsigned long long* pos, int c_hint = -1,
+                                          int split = 0) {
   int got = 0;
-  int c = c_hint >= 0 ? c_hint : ld_relaxed_s32(&m->count);
-  for (;;) {
-    int room = is_deq ? c : cap - c;
-    if (room <= 0) break;
-    int take = min(room, want);
-    int nc = is_deq ? c - take : c + take;
-    int old = atomicCAS(&m->count, c, nc);
-    if (old == c) { got = take; break; }
-    c = old;
+  if (split) {
+    int* ctr = is_deq ? &m->count : &m->used;
+    const int old = atomicAdd(ctr, is_deq ? -want : want);
+    got = is_deq ? min(max(old, 0), want) : min(max(cap - old, 0), want);
+    if (got < want) red_add_relaxed_s32(ctr, is_deq ? want - got : got - want);
+  } else {
+    int c = c_hint >= 0 ? c_hint : ld_relaxed_s32(&m->count);
+    for (;;) {
+      int room = is_deq ? c : cap - c;
+      if (room <= 0) break;
+      int take = min(room, want);
+      int nc = is_deq ? c - take : c + take;
+      int old = atomicCAS(&m->count, c, nc);
+      if (old == c) { got = take; break; }
+      c = old;
+    }
   }
   if (got) *pos = atomicAdd(is_deq ? &m->head : &m->tail, (unsigned long long)got);
   return got;
+}
+
+// Single-shot form only: after an enqueuer has published `got` items, make
+// them available to dequeuers; after a dequeuer has freed `got` slots, give
+// the places back to enqueuers.  Called by one lane after a __syncwarp.
+__device__ __forceinline__ void wq_after_put(QueueMeta* m, int got, int split) {
+  if (split && got) red_add_relaxed_s32(&m->count, got);
+}
+__device__ __forceinline__ void wq_after_take(QueueMeta* m, int got, int split) {
+  if (split && got) red_add_relaxed_s32(&m->used, -got);
 }
 
 // Publish `item` at ticket p of a sub-queue (wait for the slot's free ticket,
@@ -232,7 +278,8 @@ __device__ __forceinline__ int wq_dequeue_warp(const QueueSet& qs, int q, int wa
                                                int c_hint = -1) {
   unsigned long long pos = 0;
   int got = 0;
-  if (lane == 0) got = wq_reserve(qs.meta + q, want, true, 1 << qs.cap_log2, &pos, c_hint);
+  if (lane == 0)
+    got = wq_reserve(qs.meta + q, want, true, 1 << qs.cap_log2, &pos, c_hint, qs.split);
   got = __shfl_sync(kFullMask, got, 0);
   if (got == 0) return 0;
   pos = __shfl_sync(kFullMask, pos, 0);
@@ -241,6 +288,10 @@ __device__ __forceinline__ int wq_dequeue_warp(const QueueSet& qs, int q, int wa
     ok = wq_take(qs.slots + ((size_t)q << qs.cap_log2), qs.cap_log2, pos + lane, item,
                  spin_limit);
   if (__any_sync(kFullMask, !ok)) return -1;
+  if (qs.split) {
+    __syncwarp();
+    if (lane == 0) wq_after_take(qs.meta + q, got, 1);
+  }
   return got;
 }
 

@@ -163,6 +163,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   if (in->cycle_walk_hops) out->cycle_walk_hops = in->cycle_walk_hops;
   out->relax_atomic = in->relax_atomic;
   out->kernel_ctas = in->kernel_ctas;
+  out->queue_form = in->queue_form;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 (the shared-memory layout of the kernels)");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -179,7 +180,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK) ||
       out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30) ||
       out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_CAS ||
-      (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4))
+      (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4) ||
+      out->queue_form < BFQ_QUEUE_FORM_AUTO || out->queue_form > BFQ_QUEUE_FORM_SINGLE_SHOT)
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -377,6 +379,7 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.wide = wide_form(g, g->tune);
   a.q_alloc = g->qs.Q;
   a.cq_alloc = g->cq.Q;
+  a.qs.split = a.cq.split = g->tune.queue_form == BFQ_QUEUE_FORM_SINGLE_SHOT ? 1 : 0;
   if (a.wide) {
     // a smaller grid on a prefix of the sub-queues (the init kernel resets
     // all of them after any run that did not end cleanly)
@@ -588,16 +591,45 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
         best_t = g->tune;
       }
     }
-    if (rc == BFQ_OK) {             // the other register form, at the best parameters
-      g->tune = best_t;
-      g->tune.kernel_ctas = wide_form(g, best_t) ? 4 : 3;
+    // then, one at a time at the best parameters so far: the other register
+    // form, the other queue reservation form, and an L2 set-aside for the
+    // labels (Sec. IV's L2 sweep) of half and three quarters
+    auto try_one = [&](bfq_tune cand) {
+      if (rc != BFQ_OK) return;
+      g->tune = cand;
       const float t = time_it(kPasses);
-      if (rc == BFQ_OK && t < best) best_t = g->tune;
+      if (rc == BFQ_OK && t < best) {
+        best = t;
+        best_t = cand;
+      }
+    };
+    {
+      bfq_tune c = best_t;
+      c.kernel_ctas = wide_form(g, best_t) ? 4 : 3;
+      try_one(c);
+    }
+    {
+      bfq_tune c = best_t;
+      c.queue_form = best_t.queue_form == BFQ_QUEUE_FORM_SINGLE_SHOT ? BFQ_QUEUE_FORM_EXACT
+                                                                     : BFQ_QUEUE_FORM_SINGLE_SHOT;
+      try_one(c);
+    }
+    int max_persist = 0;
+    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
+    cudaGetLastError();
+    if (max_persist > 0) {
+      const bfq_tune base = best_t;
+      for (int pct : {50, 75}) {
+        bfq_tune c = base;
+        c.l2_persist_pct = pct;
+        try_one(c);
+      }
     }
   }
   cudaStreamSynchronize(s);
   cudaFree(dist);
   g->tune = (rc == BFQ_OK) ? best_t : keep;
+  if (g->tune.l2_persist_pct == 0) g->release_l2();
   if (out && rc == BFQ_OK) *out = best_t;
   return rc;
 }

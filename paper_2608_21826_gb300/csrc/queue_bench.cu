@@ -71,8 +71,10 @@ __device__ __forceinline__ long long bq_dequeue(const BQArgs& q, int* item, bool
   return (long long)pos;
 }
 
-// Warp-aggregated form: the active lanes of a warp form one reservation on
-// the broker count (exact, compare-and-swap) and one ticket range.
+// Warp-aggregated forms: the active lanes of a warp form one reservation and
+// one ticket range.  BFQ_QUEUE_BQ_WARP reserves on the exact broker count
+// (compare-and-swap); BFQ_QUEUE_BWD_WARP (qs.split) makes one single-shot
+// fetch-add on the count of its own side (see wq_reserve).
 __device__ __forceinline__ long long wq_enqueue_lanes(const BQArgs& q, bool active, int item,
                                                       int lane) {
   const unsigned mask = __ballot_sync(kFullMask, active);
@@ -81,7 +83,7 @@ __device__ __forceinline__ long long wq_enqueue_lanes(const BQArgs& q, bool acti
   const int rank = __popc(mask & ((1u << lane) - 1u));
   unsigned long long pos = 0;
   int got = 0;
-  if (lane == 0) got = wq_reserve(q.qs.meta, k, false, 1 << q.qs.cap_log2, &pos);
+  if (lane == 0) got = wq_reserve(q.qs.meta, k, false, 1 << q.qs.cap_log2, &pos, -1, q.qs.split);
   got = __shfl_sync(kFullMask, got, 0);
   pos = __shfl_sync(kFullMask, pos, 0);
   long long r = -1;
@@ -90,6 +92,10 @@ __device__ __forceinline__ long long wq_enqueue_lanes(const BQArgs& q, bool acti
       r = (long long)(pos + rank);
     else
       atomicOr(q.err, kStTimeout);
+  }
+  if (q.qs.split) {
+    __syncwarp();
+    if (lane == 0) wq_after_put(q.qs.meta, got, 1);
   }
   return r;
 }
@@ -102,7 +108,7 @@ __device__ __forceinline__ long long wq_dequeue_lanes(const BQArgs& q, bool acti
   const int rank = __popc(mask & ((1u << lane) - 1u));
   unsigned long long pos = 0;
   int got = 0;
-  if (lane == 0) got = wq_reserve(q.qs.meta, k, true, 1 << q.qs.cap_log2, &pos);
+  if (lane == 0) got = wq_reserve(q.qs.meta, k, true, 1 << q.qs.cap_log2, &pos, -1, q.qs.split);
   got = __shfl_sync(kFullMask, got, 0);
   pos = __shfl_sync(kFullMask, pos, 0);
   long long r = -1;
@@ -114,6 +120,10 @@ __device__ __forceinline__ long long wq_dequeue_lanes(const BQArgs& q, bool acti
     } else {
       atomicOr(q.err, kStTimeout);
     }
+  }
+  if (q.qs.split) {
+    __syncwarp();
+    if (lane == 0) wq_after_take(q.qs.meta, got, 1);
   }
   return r;
 }
@@ -130,7 +140,7 @@ __device__ void run_enqueues(const BQArgs& q, const int* items, long long n, lon
                              int part_block, int part_blocks) {
   long long i0, stride;
   op_range(n, part_block, part_blocks, &i0, &stride);
-  if (q.variant == BFQ_QUEUE_BQ_WARP) {
+  if (q.variant == BFQ_QUEUE_BQ_WARP || q.variant == BFQ_QUEUE_BWD_WARP) {
     const int lane = threadIdx.x & 31;
     // whole warps iterate together so the warp collectives stay converged
     const long long wbase0 = i0 - lane;
@@ -153,7 +163,7 @@ __device__ void run_dequeues(const BQArgs& q, int* out, long long n, long long* 
                              int part_block, int part_blocks) {
   long long i0, stride;
   op_range(n, part_block, part_blocks, &i0, &stride);
-  if (q.variant == BFQ_QUEUE_BQ_WARP) {
+  if (q.variant == BFQ_QUEUE_BQ_WARP || q.variant == BFQ_QUEUE_BWD_WARP) {
     const int lane = threadIdx.x & 31;
     const long long wbase0 = i0 - lane;
     for (long long wb = wbase0; wb < n; wb += stride) {
@@ -306,7 +316,7 @@ int bfq_queue_create(bfq_queue_t* out, int64_t capacity, int32_t variant) {
   *out = nullptr;
   if (capacity < 1 || capacity > (1LL << 30))
     return q_invalid("bfq_queue_create: capacity must be in [1, 2^30]");
-  if (variant < BFQ_QUEUE_BQ || variant > BFQ_QUEUE_BQ_WARP)
+  if (variant < BFQ_QUEUE_BQ || variant > BFQ_QUEUE_BWD_WARP)
     return q_invalid("bfq_queue_create: unknown variant");
   bfq_queue* q = new (std::nothrow) bfq_queue();
   if (!q) return q_invalid("bfq_queue_create: host allocation failed");
@@ -315,13 +325,14 @@ int bfq_queue_create(bfq_queue_t* out, int64_t capacity, int32_t variant) {
   a.variant = variant;
   a.spin_limit = 1LL << 22;
   int rc = q->alloc((void**)&a.err, sizeof(int));
-  if (!rc && variant == BFQ_QUEUE_BQ_WARP) {
+  if (!rc && (variant == BFQ_QUEUE_BQ_WARP || variant == BFQ_QUEUE_BWD_WARP)) {
     int l = 0;
     while ((1LL << l) < capacity) ++l;
     q->N = 1LL << l;
     a.N = q->N;
     a.qs.Q = 1;
     a.qs.cap_log2 = l;
+    a.qs.split = variant == BFQ_QUEUE_BWD_WARP ? 1 : 0;
     rc = q->alloc((void**)&a.qs.meta, sizeof(QueueMeta));
     if (!rc) rc = q->alloc((void**)&a.qs.slots, sizeof(unsigned long long) * (size_t)q->N);
   } else if (!rc) {
@@ -348,7 +359,7 @@ int bfq_queue_reset(bfq_queue_t q, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   BQArgs& a = q->args;
   BFQ_CUDA_TRY(cudaMemsetAsync(a.err, 0, sizeof(int), s));
-  if (q->variant == BFQ_QUEUE_BQ_WARP) {
+  if (q->variant == BFQ_QUEUE_BQ_WARP || q->variant == BFQ_QUEUE_BWD_WARP) {
     BFQ_CUDA_TRY(cudaMemsetAsync(a.qs.meta, 0, sizeof(QueueMeta), s));
     BFQ_CUDA_TRY(cudaMemsetAsync(a.qs.slots, 0, sizeof(unsigned long long) * (size_t)q->N, s));
   } else {
@@ -407,7 +418,7 @@ int bfq_queue_state(bfq_queue_t q, int64_t* head, int64_t* tail, int64_t* count,
   int err = 0;
   long long h = 0, t = 0, c = 0;
   BFQ_CUDA_TRY(cudaMemcpy(&err, q->args.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (q->variant == BFQ_QUEUE_BQ_WARP) {
+  if (q->variant == BFQ_QUEUE_BQ_WARP || q->variant == BFQ_QUEUE_BWD_WARP) {
     QueueMeta m;
     BFQ_CUDA_TRY(cudaMemcpy(&m, q->args.qs.meta, sizeof(m), cudaMemcpyDeviceToHost));
     h = (long long)m.head;

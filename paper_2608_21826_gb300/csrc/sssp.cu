@@ -42,41 +42,46 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 }
 
 // Relax the merged edge lists of the items held by lanes [0, n): lane j owns
-// edges [beg_j, beg_j + deg_j) of a tail whose label is lab_j.  Edges are
-// walked lane-contiguously, U groups of 32 per step so that the loads of
-// the groups overlap.  Returns false on a timeout.
+// edges [beg_j, beg_j + deg_j) of a tail whose label is lab_j.  The items
+// with edges are staged in shared memory (BatchStage) and the edges walked
+// lane-contiguously, U groups of 32 per step so that the loads of the
+// groups overlap.  Returns false on a timeout.
 // Claimed children are appended to the warp's buffer `buf` (nbuf items,
 // capacity kChildBuf) and published in bulk by flush_children.
 template <int U, bool MIN>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
                                              long long lab, int tail, int lane, int home,
-                                             WarpCounters& wc, unsigned* buf, int& nbuf,
-                                             unsigned& walk_at) {
+                                             WarpCounters& wc, unsigned& upd, unsigned* buf,
+                                             int& nbuf, unsigned& walk_at, BatchStage* st) {
+  const bool has = lane < n && deg > 0;
+  const unsigned hm = __ballot_sync(kFullMask, has);
+  if (!hm) return true;
   int total = 0;
-  const int excl = warp_excl_scan(deg, lane, &total);
-  wc.rel += (lane == 0) ? (unsigned)total : 0u;
+  const int excl = warp_excl_scan(has ? deg : 0, lane, &total);
+  if (lane == 0) wc.rel += (unsigned)total;
+  if (has) {
+    const int r = __popc(hm & lanemask_lt());
+    st->key0[r] = pack_label(label_dist(lab), label_hops(lab) + 1u);
+    st->off[r] = beg - excl;
+    st->tail[r] = tail;
+  }
+  __syncwarp();
   const unsigned V = (unsigned)a.V;
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
-    long long lab_t[U];
-    int tl[U];
+    int own[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       act[g] = false;
       cw[g] = make_int2(0, 0);
-      lab_t[g] = 0;
-      tl[g] = 0;
-      if (base + 32 * g < total) {          // warp-uniform
-        const int t = base + 32 * g + lane;
-        const int j = owner_lane(excl, t, n);
-        const int ex_j = __shfl_sync(kFullMask, excl, j);
-        const int beg_j = __shfl_sync(kFullMask, beg, j);
-        lab_t[g] = __shfl_sync(kFullMask, lab, j);
-        tl[g] = __shfl_sync(kFullMask, tail, j);
-        if (t < total) {
+      own[g] = 0;
+      const int P = base + 32 * g;
+      if (P < total) {                      // warp-uniform
+        own[g] = staged_owner(has, excl, P);
+        if (P + lane < total) {
           act[g] = true;
-          cw[g] = __ldg(&a.adj[beg_j + (t - ex_j)]);
+          cw[g] = __ldg(&a.adj[st->off[own[g]] + P + lane]);
         }
       }
     }
@@ -86,18 +91,9 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       key[g] = 0;
       cur[g] = 0;
       if (act[g]) {
-        const long long nd = (long long)label_dist(lab_t[g]) + (long long)cw[g].y;
-        if (label_dist(lab_t[g]) == kNegInf32) {
-          // minus-infinity tail (only when cycles are resolved): so is the head
-          key[g] = kNegInfLabel;
-        } else if (nd >= (long long)kInf32) {
-          act[g] = false;
-        } else if (nd <= -2147483648LL) {
-          raise_status(a.ctl, kStRange);
-          act[g] = false;
-        } else {
-          key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
-        }
+        const int c = edge_candidate(st->key0[own[g]], cw[g].y, &key[g]);
+        if (c < 0) raise_status(a.ctl, kStRange);
+        act[g] = c > 0;
         if (act[g] && !MIN) cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
       }
     }
@@ -129,23 +125,21 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       }
     }
     bool enq[U];
-    unsigned item[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       enq[g] = false;
-      item[g] = (unsigned)cw[g].x;
       if (act[g]) {
         const int r =
             MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
                         : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
                                               : lower_label(&a.label[cw[g].x], key[g], prev[g]);
         if (r) {
-          ++wc.upd;
+          ++upd;
           const unsigned nh = label_hops(key[g]);
           bool proven = nh >= V;          // a walk of >= V edges that still improved
           if (!proven && a.cyc && nh >= (a.cyc_walk0 >> 1)) {
             st_relaxed_u64((unsigned long long*)(a.cyc + cw[g].x),
-                           (unsigned long long)pack_edge(tl[g], cw[g].y));
+                           (unsigned long long)pack_edge(st->tail[own[g]], cw[g].y));
             if (nh >= walk_at) {
               if (prove_negative_cycle(a.cyc, a.label, cw[g].x, a.V))
                 proven = true;
@@ -175,11 +169,12 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         if (nbuf + __popc(m) > kChildBuf) {
           if (!flush_children(a, home, buf, nbuf, lane, wc)) return false;
         }
-        if (enq[g]) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = item[g];
+        if (enq[g]) buf[nbuf + __popc(m & lanemask_lt())] = (unsigned)cw[g].x;
         nbuf += __popc(m);
       }
     }
   }
+  __syncwarp();                         // stage free for the next batch
   return true;
 }
 
@@ -188,7 +183,8 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
 template <bool MIN>
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
                                             int home, int chome, WarpCounters& wc,
-                                            unsigned* buf, int& nbuf, unsigned& walk_at) {
+                                            unsigned& upd, unsigned* buf, int& nbuf,
+                                            unsigned& walk_at, BatchStage* st) {
   int K = 0;
   const int excl = warp_excl_scan(nch, lane, &K);
   if (K == 0) return true;
@@ -220,8 +216,8 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
         tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
-                                 walk_at) ||
+      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, upd, buf,
+                                      nbuf, walk_at, st) ||
           !flush_children(a, home, buf, nbuf, lane, wc))
         return false;
       if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -1);
@@ -246,14 +242,23 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
   const int home = (blockIdx.x * a.queues_per_cta + wid % a.queues_per_cta) % a.qs.Q;
   const int chome = blockIdx.x % a.cq.Q;
   const int share = a.share_div > 0 ? a.share_div : max(1, nwarps / a.queues_per_cta);
-  WarpCounters wc;
-  const unsigned long long t_start = globaltimer_ns();
+  // warp statistics live in shared memory (lane 0 keeps them; only the
+  // per-lane update count stays in a register) to spare registers
+  __shared__ WarpCounters s_wc[kBlock / 32];
+  __shared__ unsigned long long s_t_start;
+  WarpCounters& wc = s_wc[wid];
+  if (lane == 0) wc = WarpCounters();
+  if (threadIdx.x == 0) s_t_start = globaltimer_ns();
+  __syncthreads();
+  unsigned upd = 0;
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
   bool timed_out = false;
 
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
+  __shared__ BatchStage s_stage[kBlock / 32];
   unsigned* buf = s_children[wid];
+  BatchStage* st = &s_stage[wid];
   int nbuf = 0;
   unsigned walk_at = a.cyc_walk0;     // per lane: hops that trigger a cycle walk
   for (;;) {
@@ -262,11 +267,15 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
     bool is_chunk = false;
     // hub chunks first (they sit on the critical path), then the own vertex
     // sub-queue, then stealing; both home counts are read in one step
+    // (the stop flag is read in the same step, so retiring a batch needs no
+    // load of its own)
     int c = 0;
     if (lane == 0) c = ld_relaxed_s32(&a.cq.meta[chome].count);
     else if (lane == 1) c = ld_relaxed_s32(&a.qs.meta[home].count);
+    else if (lane == 2) c = ld_relaxed_s32(&a.ctl->stop);
     const int c_chunk = __shfl_sync(kFullMask, c, 0);
     const int c_vert = __shfl_sync(kFullMask, c, 1);
+    if (__shfl_sync(kFullMask, c, 2)) break;
     if (c_chunk > 0) {
       is_chunk = true;
       got = wq_dequeue_warp(a.cq, chome, a.chunk_batch, lane, &item, a.spin_limit, c_chunk);
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
                                   a.spin_limit, cq_cnt);
         }
       }
-      if (got > 0) ++wc.steal;
+      if (got > 0 && lane == 0) ++wc.steal;
     }
     if (got < 0) { timed_out = true; break; }
     if (got == 0) {
@@ -302,19 +311,21 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
       if (lane == 0)
         done = (ld_relaxed_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
       if (__shfl_sync(kFullMask, done, 0)) break;
-      ++wc.idle;
+      if (lane == 0) ++wc.idle;
       __nanosleep(min(32u << min(idle, 6), 2048u));
       ++idle;
       if ((idle & 31) == 0 &&
-          (long long)(globaltimer_ns() - t_start) > a.time_limit_ns) {
+          (long long)(globaltimer_ns() - s_t_start) > a.time_limit_ns) {
         timed_out = true;
         break;
       }
       continue;
     }
     idle = 0;
-    wc.deq += (lane == 0) ? (unsigned)got : 0u;
-    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned)got : 0u;
+    if (lane == 0) {
+      wc.deq += (unsigned)got;
+      if (is_chunk) wc.chunk += (unsigned)got;
+    }
 
     int beg = 0, deg = 0, nch = 0, c0 = 0, tail = 0;
     long long lab = 0;
@@ -342,13 +353,13 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at)) {
+      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, upd, buf, nbuf, walk_at, st)) {
         timed_out = true;
         break;
       }
     }
-    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
-                               walk_at) ||
+    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, upd, buf,
+                                    nbuf, walk_at, st) ||
         !flush_children(a, home, buf, nbuf, lane, wc)) {
       timed_out = true;
       break;
@@ -356,16 +367,11 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
     // retire the batch.  Its children were counted by this lane earlier, on
     // the same counter, so coherence orders this decrement after them; the
     // labels are read by the epilogue kernel, after this kernel has ended.
-    int stop = 0;
-    if (lane == 0) {
-      red_add_relaxed_s32(&a.ctl->inflight, -got);
-      stop = ld_relaxed_s32(&a.ctl->stop);
-    }
-    if (__shfl_sync(kFullMask, stop, 0)) break;
+    if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -got);
   }
   if (timed_out && lane == 0) raise_status(a.ctl, kStTimeout);
 
-  const unsigned long long upd_sum = warp_sum_u64(wc.upd);
+  const unsigned long long upd_sum = warp_sum_u64(upd);
   if (lane == 0) {
     if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], (unsigned long long)wc.deq);
     if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], (unsigned long long)wc.rel);
@@ -428,11 +434,13 @@ __global__ void sssp_init_kernel(SsspArgs a) {
     for (long long i = tid; i < ncslots; i += nth) a.cq.slots[i] = 0ull;
     for (long long q = tid; q < q_all; q += nth) {
       a.qs.meta[q].count = (q == 0) ? 1 : 0;
+      a.qs.meta[q].used = (q == 0) ? 1 : 0;
       a.qs.meta[q].head = 0;
       a.qs.meta[q].tail = (q == 0) ? 1 : 0;
     }
     for (long long q = tid; q < cq_all; q += nth) {
       a.cq.meta[q].count = 0;
+      a.cq.meta[q].used = 0;
       a.cq.meta[q].head = 0;
       a.cq.meta[q].tail = 0;
     }
@@ -444,6 +452,7 @@ __global__ void sssp_init_kernel(SsspArgs a) {
         ((unsigned long long)(2u * lap + 1u) << 32) | (unsigned)a.src;
     m->tail = p + 1;
     m->count = 1;
+    m->used = 1;          // one place taken (single-shot form; unused otherwise)
   }
   if (tid == 0) {
     a.ctl->inflight = 1 + a.phantom;
@@ -525,6 +534,7 @@ __global__ void queue_reset_kernel(QueueSet qs) {
   for (long long i = tid; i < n; i += nth) qs.slots[i] = 0ull;
   for (long long q = tid; q < qs.Q; q += nth) {
     qs.meta[q].count = 0;
+    qs.meta[q].used = 0;
     qs.meta[q].head = 0;
     qs.meta[q].tail = 0;
   }

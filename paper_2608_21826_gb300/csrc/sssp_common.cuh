@@ -50,6 +50,58 @@ __device__ __forceinline__ int owner_lane(int excl, int t, int n) {
   return j;
 }
 
+__device__ __forceinline__ unsigned lanemask_le() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// A warp's batch staged for the merged edge walk.  The items that have
+// edges to relax are compacted, in lane order, into slots 0..k-1; edge t of
+// the merged list (positions excl_j .. excl_j + deg_j - 1 belong to the
+// item of lane j) is adj[off[r] + t] for the item's slot r, and key0[r] is
+// (dist, hops + 1) of the item's tail label, the candidate key before the
+// edge weight is added.
+struct BatchStage {
+  long long key0[32];
+  int off[32];
+  int tail[32];
+};
+
+// Slot (in the compacted order) of the item that owns position P + lane of
+// the merged list, for a warp-uniform P.  has/excl are the lane's item flag
+// and exclusive edge prefix; slots are consecutive along the list, so the
+// owner is the slot of position P plus the number of item starts in
+// (P, P + lane], read from a 32-bit mask of the starts in (P, P + 32).
+__device__ __forceinline__ int staged_owner(bool has, int excl, int P) {
+  const unsigned bit = (has && excl > P && excl < P + 32) ? (1u << (excl - P)) : 0u;
+  const unsigned starts = __reduce_or_sync(kFullMask, bit);
+  const int o0 = __popc(__ballot_sync(kFullMask, has && excl <= P)) - 1;
+  return o0 + __popc(starts & lanemask_le());
+}
+
+// Candidate label of an edge of weight w out of a tail whose key0 is
+// (dist, hops + 1): (dist + w, hops + 1), or minus infinity from a
+// minus-infinity tail.  Returns 0 (no candidate: dist + w cannot be stored),
+// 1 (candidate in *key) or -1 (dist + w is below the int32 range).
+__device__ __forceinline__ int edge_candidate(long long key0, int w, long long* key) {
+  const int d = label_dist(key0);
+  if (d == kNegInf32) {
+    *key = kNegInfLabel;
+    return 1;
+  }
+  const long long nd = (long long)d + (long long)w;
+  if (nd >= (long long)kInf32) return 0;
+  if (nd <= -2147483648LL) return -1;
+  *key = key0 + (long long)((unsigned long long)(long long)w << 32);
+  return 1;
+}
+
 // Lanes probe up to 64 sub-queues starting at `start`; returns the fullest
 // non-empty one seen, or -1.
 __device__ __forceinline__ int probe_queues(const QueueSet& qs, int start, int skip, int lane) {
@@ -83,7 +135,7 @@ __device__ __forceinline__ int enqueue_warp(const QueueSet& qs, int home, bool a
   for (long long tries = 0; done < k && tries < max_tries; ++tries) {
     unsigned long long pos = 0;
     int got = 0;
-    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos);
+    if (lane == 0) got = wq_reserve(qs.meta + q, k - done, false, cap, &pos, -1, qs.split);
     got = __shfl_sync(kFullMask, got, 0);
     if (got) {
       pos = __shfl_sync(kFullMask, pos, 0);
@@ -93,6 +145,7 @@ __device__ __forceinline__ int enqueue_warp(const QueueSet& qs, int home, bool a
         ok = wq_put(qs.slots + ((size_t)q << qs.cap_log2), qs.cap_log2, pos + r, item,
                     spin_limit);
       if (__any_sync(kFullMask, !ok)) return -1;
+      if (lane == 0) wq_after_put(qs.meta + q, got, qs.split);
       done += got;
     }
     q = (q + 1 == qs.Q) ? 0 : q + 1;
@@ -121,7 +174,7 @@ __device__ __forceinline__ bool enqueue_buffer(const QueueSet& qs, int home,
   for (long long tries = 0; done < count && tries < max_tries; ++tries) {
     unsigned long long pos = 0;
     int got = 0;
-    if (lane == 0) got = wq_reserve(qs.meta + q, count - done, false, cap, &pos);
+    if (lane == 0) got = wq_reserve(qs.meta + q, count - done, false, cap, &pos, -1, qs.split);
     got = __shfl_sync(kFullMask, got, 0);
     if (got) {
       pos = __shfl_sync(kFullMask, pos, 0);
@@ -130,6 +183,7 @@ __device__ __forceinline__ bool enqueue_buffer(const QueueSet& qs, int home,
       for (int i = lane; i < got; i += 32)
         ok = wq_put(qslots, qs.cap_log2, pos + i, buf[done + i], spin_limit) && ok;
       if (__any_sync(kFullMask, !ok)) return false;
+      if (lane == 0) wq_after_put(qs.meta + q, got, qs.split);
       done += got;
     }
     q = (q + 1 == qs.Q) ? 0 : q + 1;

@@ -120,3 +120,76 @@ def test_check_fifo_positions_rejects_mismatch():
     assert bq.check_fifo_positions([1, 2], [0, 1], [1, 2], [1, 0]) is not None
     assert bq.check_fifo_positions([1, 2], [0, 2], [], []) is not None
     assert bq.check_fifo_positions([1], [0], [1, 1], [0, 1]) is not None
+
+
+def _warp_run(form, seed, n_warps=12, N=16, k_max=8, rounds=3):
+    """Warps alternately enqueue and dequeue batches of up to k_max items,
+    interleaved at random; returns (results, ops) or raises on a stall."""
+    rng = random.Random(seed)
+    q = bq.WarpQueueSim(N, form)
+    ops = []
+    nxt = 0
+    for w in range(n_warps):
+        for r in range(rounds):
+            if (w + r) % 2 == 0:
+                k = rng.randint(1, k_max)
+                ops.append(("enq", q.enqueue_warp(list(range(nxt, nxt + k)))))
+                nxt += k
+            else:
+                ops.append(("deq", q.dequeue_warp(rng.randint(1, k_max))))
+    rng.shuffle(ops)
+    return q, ops, bq.run_interleaved(q, ops, seed)
+
+
+@pytest.mark.parametrize("form", ["exact", "split"])
+@pytest.mark.parametrize("seed", range(40))
+def test_warp_forms_interleaved(form, seed):
+    """The warp-aggregated forms: no wait is ever stranded (the run ends),
+    every dequeued item was enqueued at the same ticket position, positions
+    are gap-free, and the counters end consistent with the ring."""
+    q, ops, res = _warp_run(form, seed)
+    enq_items, enq_pos, deq_items, deq_pos = [], [], [], []
+    for (kind, _), out in zip(ops, res):
+        for item, p in out:
+            (enq_items if kind == "enq" else deq_items).append(item)
+            (enq_pos if kind == "enq" else deq_pos).append(p)
+    assert bq.check_fifo_positions(enq_items, enq_pos, deq_items, deq_pos) is None
+    held = len(enq_pos) - len(deq_pos)
+    assert q.tail - q.head == held
+    if form == "exact":
+        assert q.count == held
+    else:
+        assert q.avail == held and q.free == q.N - held
+
+
+def test_warp_forms_drain_what_they_hold():
+    """After concurrent traffic, every item still held comes out, in ticket
+    order, for both forms."""
+    for form in ("exact", "split"):
+        q, ops, res = _warp_run(form, 5)
+        left = q.tail - q.head
+        out = bq.run_interleaved(q, [("deq", q.dequeue_warp(q.N))], 0)[0]
+        assert len(out) == left
+        assert [p for _, p in out] == list(range(q.head - left, q.head))
+
+
+def test_naive_single_count_can_strand_a_dequeuer():
+    """One count moved by fetch-add, the surplus added back afterwards: in
+    the window an enqueuer's withdrawn surplus is visible to dequeuers, a
+    dequeuer is granted items that no enqueuer will ever publish, and its
+    ticket wait never ends even after everyone else has finished.  The
+    single-shot form keeps two counters for this reason; both proper forms
+    end the same schedule."""
+    for form in ("naive", "split", "exact"):
+        q = bq.WarpQueueSim(4, form)
+        bq.run_interleaved(q, [("enq", q.enqueue_warp([1, 2, 3, 4]))], 0)   # full
+        big = q.enqueue_warp([10, 11, 12, 13])     # no room: must withdraw
+        next(big)                                  # its reservation step
+        thief = q.dequeue_warp(8)
+        next(thief)                                # its reservation, before the withdrawal
+        if form == "naive":
+            with pytest.raises(RuntimeError, match="stalled"):
+                bq.run_interleaved(q, [("deq", thief), ("enq", big)], 0)
+        else:
+            res = bq.run_interleaved(q, [("deq", thief), ("enq", big)], 0)
+            assert [x for x, _ in res[0]] == [1, 2, 3, 4] and res[1] == []

@@ -8,8 +8,10 @@ from oracle import broker_queue as bq
 from paper_2608_21826_gb300 import bfq
 
 pytestmark = pytest.mark.gpu
-VARIANTS = [bfq.QUEUE_BQ, bfq.QUEUE_BWD, bfq.QUEUE_BQ_WARP]
-VNAMES = {bfq.QUEUE_BQ: "bq", bfq.QUEUE_BWD: "bwd", bfq.QUEUE_BQ_WARP: "bq_warp"}
+VARIANTS = [bfq.QUEUE_BQ, bfq.QUEUE_BWD, bfq.QUEUE_BQ_WARP, bfq.QUEUE_BWD_WARP]
+VNAMES = {bfq.QUEUE_BQ: "bq", bfq.QUEUE_BWD: "bwd", bfq.QUEUE_BQ_WARP: "bq_warp",
+          bfq.QUEUE_BWD_WARP: "bwd_warp"}
+WARP = (bfq.QUEUE_BQ_WARP, bfq.QUEUE_BWD_WARP)
 
 
 def _t(a):
@@ -74,7 +76,7 @@ def test_full_and_empty_counts(variant):
 @pytest.mark.parametrize("variant", VARIANTS, ids=VNAMES.get)
 def test_wraparound_many_laps(variant):
     import torch
-    N = 1000 if variant != bfq.QUEUE_BQ_WARP else 1024
+    N = 1000 if variant not in WARP else 1024
     q = bfq.bfq_queue_create(N, variant)
     try:
         for lap in range(7):

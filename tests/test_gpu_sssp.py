@@ -132,6 +132,10 @@ def test_rmat22_full_all_sources():
     dict(kernel_ctas=4),
     dict(kernel_ctas=3, relax_atomic=2, hub_degree=32, chunk_edges=32, batch_items=4),
     dict(kernel_ctas=3, ctas_per_sm=2, queues_per_cta=2),
+    dict(queue_form=2),
+    dict(queue_form=2, kernel_ctas=3),
+    dict(queue_form=2, hub_degree=32, chunk_edges=32, batch_items=4, queues_per_cta=4),
+    dict(queue_form=2, relax_atomic=2, ctas_per_sm=1),
 ], ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
 def test_tunes(tune):
     g = synth.workload_rmat(14)
@@ -369,3 +373,25 @@ def test_cycle_walk_threshold_validated():
     for bad in (1, -3, (1 << 30) + 1):
         with pytest.raises(bfq.BfqError):
             gpu_util.create(g, bfq.make_tune(cycle_walk_hops=bad))
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_queue_forms_full_size_and_cycles(form):
+    """The exact-count (1) and single-shot (2) worklist reservations give
+    the oracle's results on the road-like grid, R-MAT 16 and a planted
+    cycle, and a switch between them on one handle meets no stale queue
+    state."""
+    road = synth.workload_road1m()
+    rm = synth.workload_rmat(16)
+    cyc = synth.plant_negative_cycle(synth.grid_graph(50, 50, seed=3), 5, seed=2)
+    for g, srcs in ((road, road.sources[:2]), (rm, rm.sources[:2]), (cyc, [0])):
+        h = gpu_util.create(g, bfq.make_tune(queue_form=form))
+        try:
+            for s in srcs:
+                _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
+            t = bfq.bfq_graph_get_tune(h)
+            t.queue_form = 3 - form
+            bfq.bfq_graph_set_tune(h, t)
+            _compare(g, int(srcs[0]), gpu_util.run(h, g.V, int(srcs[0])))
+        finally:
+            bfq.bfq_graph_destroy(h)
