@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
   extern __shared__ int s_off[];                // loff[nq+1], coff[nq+1]
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   __shared__ unsigned short s_childq[kBlock / 32][kChildBuf];
+  __shared__ MultiStage s_mstage[kBlock / 32];
   const StageHeader hdr = *a.hdr;
   const int nq = hdr.nq;
   int* s_loff = s_off;
@@ -173,11 +174,15 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
     unsigned item = 0;
     int got = 0;
     bool is_chunk = false;
+    // (the stop flag is read in the same step, so retiring a batch needs no
+    // load of its own)
     int c = 0;
     if (lane == 0) c = ld_relaxed_s32(&a.cq.meta[chome].count);
     else if (lane == 1) c = ld_relaxed_s32(&a.qs.meta[home].count);
+    else if (lane == 2) c = ld_relaxed_s32(&a.ctl->stop);
     const int c_chunk = __shfl_sync(kFullMask, c, 0);
     const int c_vert = __shfl_sync(kFullMask, c, 1);
+    if (__shfl_sync(kFullMask, c, 2)) break;
     if (c_chunk > 0) {
       is_chunk = true;
       got = wq_dequeue_warp(a.cq, chome, hdr.chunk_batch, lane, &item, hdr.spin_limit, c_chunk);
@@ -305,8 +310,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
             cV = d.V;
             ctail = ct.x;
           }
-          if (!relax_multi<kGroups, MIN>(env, 1, cep, cdeg, clab, clb, cV, cq_q, ctail, lane, home,
-                                    wc, buf, bufq, nbuf, walk_at) ||
+          if (!relax_multi<kMultiGroups, MIN>(env, 1, cep, cdeg, clab, clb, cV, cq_q, ctail, lane, home,
+                                    wc, buf, bufq, nbuf, walk_at, &s_mstage[wid]) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             timed_out = true;
             break;
@@ -317,8 +322,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
       }
       if (timed_out) break;
     }
-    if (!relax_multi<kGroups, MIN>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
-                              buf, bufq, nbuf, walk_at) ||
+    if (!relax_multi<kMultiGroups, MIN>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+                              buf, bufq, nbuf, walk_at, &s_mstage[wid]) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       timed_out = true;
       break;
@@ -335,9 +340,6 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
       timed_out = true;
       break;
     }
-    int stop = 0;
-    if (lane == 0) stop = ld_relaxed_s32(&a.ctl->stop);
-    if (__shfl_sync(kFullMask, stop, 0)) break;
   }
   if (timed_out && lane == 0) batch_timeout(a);
   const unsigned long long upd_sum = warp_sum_u64(wc.upd);

@@ -614,6 +614,17 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
                                                                      : BFQ_QUEUE_FORM_SINGLE_SHOT;
       try_one(c);
     }
+    {
+      // the other relaxation form (atomicMin pays while the labels stay in
+      // L2; near the half-of-L2 rule either may win)
+      bfq_tune c = best_t;
+      const bool min_now =
+          best_t.relax_atomic == BFQ_RELAX_MIN ||
+          (best_t.relax_atomic == BFQ_RELAX_AUTO &&
+           (long long)sizeof(long long) * g->V <= g->l2_bytes / 2);
+      c.relax_atomic = min_now ? BFQ_RELAX_CAS : BFQ_RELAX_MIN;
+      try_one(c);
+    }
     int max_persist = 0;
     cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
     cudaGetLastError();

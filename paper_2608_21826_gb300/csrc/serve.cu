@@ -310,6 +310,7 @@ __device__ __forceinline__ bool run_task(const ServeArgs& a, unsigned id, int la
 __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) serve_kernel(ServeArgs a) {
   __shared__ unsigned s_children[kBlock / 32][kChildBuf];
   __shared__ unsigned short s_childq[kBlock / 32][kChildBuf];
+  __shared__ MultiStage s_mstage[kBlock / 32];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -514,8 +515,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) serve_kernel(Se
             cV = d.V;
             ctail = ct.x;
           }
-          if (!relax_multi<kGroups, false>(env, 1, cep, cdeg, clab, clb, cV, cs, ctail, lane, home, wc,
-                                    buf, bufq, nbuf, walk_at) ||
+          if (!relax_multi<kMultiGroups, false>(env, 1, cep, cdeg, clab, clb, cV, cs, ctail, lane, home, wc,
+                                    buf, bufq, nbuf, walk_at, &s_mstage[wid]) ||
               !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
             failed = true;
             break;
@@ -526,8 +527,8 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) serve_kernel(Se
       }
       if (failed) break;
     }
-    if (!relax_multi<kGroups, false>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
-                              buf, bufq, nbuf, walk_at) ||
+    if (!relax_multi<kMultiGroups, false>(env, got, eptr, deg, lab, lbase, Vq, q, tail, lane, home, wc,
+                              buf, bufq, nbuf, walk_at, &s_mstage[wid]) ||
         !flush_multi(env, home, buf, bufq, nbuf, lane, wc)) {
       failed = true;
       break;

@@ -51,14 +51,14 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 template <int U, bool MIN>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
                                              long long lab, int tail, int lane, int home,
-                                             WarpCounters& wc, unsigned& upd, unsigned* buf,
-                                             int& nbuf, unsigned& walk_at, BatchStage* st) {
+                                             WarpCounters& wc, unsigned* buf, int& nbuf,
+                                             unsigned& walk_at, BatchStage* st) {
   const bool has = lane < n && deg > 0;
   const unsigned hm = __ballot_sync(kFullMask, has);
   if (!hm) return true;
   int total = 0;
   const int excl = warp_excl_scan(has ? deg : 0, lane, &total);
-  if (lane == 0) wc.rel += (unsigned)total;
+  wc.rel += (lane == 0) ? (unsigned)total : 0u;
   if (has) {
     const int r = __popc(hm & lanemask_lt());
     st->key0[r] = pack_label(label_dist(lab), label_hops(lab) + 1u);
@@ -134,7 +134,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
                         : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
                                               : lower_label(&a.label[cw[g].x], key[g], prev[g]);
         if (r) {
-          ++upd;
+          ++wc.upd;
           const unsigned nh = label_hops(key[g]);
           bool proven = nh >= V;          // a walk of >= V edges that still improved
           if (!proven && a.cyc && nh >= (a.cyc_walk0 >> 1)) {
@@ -183,8 +183,8 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
 template <bool MIN>
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
                                             int home, int chome, WarpCounters& wc,
-                                            unsigned& upd, unsigned* buf, int& nbuf,
-                                            unsigned& walk_at, BatchStage* st) {
+                                            unsigned* buf, int& nbuf, unsigned& walk_at,
+                                            BatchStage* st) {
   int K = 0;
   const int excl = warp_excl_scan(nch, lane, &K);
   if (K == 0) return true;
@@ -216,8 +216,8 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
         tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, upd, buf,
-                                      nbuf, walk_at, st) ||
+      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+                                      walk_at, st) ||
           !flush_children(a, home, buf, nbuf, lane, wc))
         return false;
       if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -1);
@@ -242,15 +242,8 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
   const int home = (blockIdx.x * a.queues_per_cta + wid % a.queues_per_cta) % a.qs.Q;
   const int chome = blockIdx.x % a.cq.Q;
   const int share = a.share_div > 0 ? a.share_div : max(1, nwarps / a.queues_per_cta);
-  // warp statistics live in shared memory (lane 0 keeps them; only the
-  // per-lane update count stays in a register) to spare registers
-  __shared__ WarpCounters s_wc[kBlock / 32];
-  __shared__ unsigned long long s_t_start;
-  WarpCounters& wc = s_wc[wid];
-  if (lane == 0) wc = WarpCounters();
-  if (threadIdx.x == 0) s_t_start = globaltimer_ns();
-  __syncthreads();
-  unsigned upd = 0;
+  WarpCounters wc;
+  const unsigned long long t_start = globaltimer_ns();
   unsigned rng = 0x9e3779b9u * (blockIdx.x * 64u + wid + 1u);
   int idle = 0;
   bool timed_out = false;
@@ -303,7 +296,7 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
                                   a.spin_limit, cq_cnt);
         }
       }
-      if (got > 0 && lane == 0) ++wc.steal;
+      if (got > 0) ++wc.steal;
     }
     if (got < 0) { timed_out = true; break; }
     if (got == 0) {
@@ -311,21 +304,19 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
       if (lane == 0)
         done = (ld_relaxed_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
       if (__shfl_sync(kFullMask, done, 0)) break;
-      if (lane == 0) ++wc.idle;
+      ++wc.idle;
       __nanosleep(min(32u << min(idle, 6), 2048u));
       ++idle;
       if ((idle & 31) == 0 &&
-          (long long)(globaltimer_ns() - s_t_start) > a.time_limit_ns) {
+          (long long)(globaltimer_ns() - t_start) > a.time_limit_ns) {
         timed_out = true;
         break;
       }
       continue;
     }
     idle = 0;
-    if (lane == 0) {
-      wc.deq += (unsigned)got;
-      if (is_chunk) wc.chunk += (unsigned)got;
-    }
+    wc.deq += (lane == 0) ? (unsigned)got : 0u;
+    if (is_chunk) wc.chunk += (lane == 0) ? (unsigned)got : 0u;
 
     int beg = 0, deg = 0, nch = 0, c0 = 0, tail = 0;
     long long lab = 0;
@@ -353,13 +344,13 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, upd, buf, nbuf, walk_at, st)) {
+      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at, st)) {
         timed_out = true;
         break;
       }
     }
-    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, upd, buf,
-                                    nbuf, walk_at, st) ||
+    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+                                    walk_at, st) ||
         !flush_children(a, home, buf, nbuf, lane, wc)) {
       timed_out = true;
       break;
@@ -371,7 +362,7 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
   }
   if (timed_out && lane == 0) raise_status(a.ctl, kStTimeout);
 
-  const unsigned long long upd_sum = warp_sum_u64(upd);
+  const unsigned long long upd_sum = warp_sum_u64(wc.upd);
   if (lane == 0) {
     if (wc.deq) atomicAdd(&a.ctl->ctr[kCtrDeq], (unsigned long long)wc.deq);
     if (wc.rel) atomicAdd(&a.ctl->ctr[kCtrRel], (unsigned long long)wc.rel);

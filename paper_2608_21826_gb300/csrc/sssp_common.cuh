@@ -208,7 +208,7 @@ __device__ __forceinline__ int lower_label(long long* label_v, long long key, lo
 }
 
 #ifndef BFQ_EDGE_GROUPS
-#define BFQ_EDGE_GROUPS 4
+#define BFQ_EDGE_GROUPS 2
 #endif
 constexpr int kGroups = BFQ_EDGE_GROUPS;   // edge groups of 32 in flight per warp step
 

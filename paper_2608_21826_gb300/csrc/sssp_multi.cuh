@@ -5,17 +5,23 @@
 
 #include "sssp_common.cuh"
 
-// The multi-query kernels (batched, serving) keep more state per warp: their
-// registers are sized for 3 CTAs per SM (80 per thread), which halves their
-// spills (the batched mix: 45 against 48 ms per launch at 4 CTAs per SM).
+// Registers of the multi-query kernels (batched, serving) and edge groups of
+// their merged walk.  With the staged walk (per-query fields in shared
+// memory, not in registers) 4 CTAs per SM at 64 registers and 2 groups in
+// flight are fastest on the batched mix (34.6 ms per launch against 39.8 at
+// 3 CTAs per SM with 3 groups).
 #ifndef BFQ_MULTI_CTAS_PER_SM
-#define BFQ_MULTI_CTAS_PER_SM 3
+#define BFQ_MULTI_CTAS_PER_SM 4
+#endif
+#ifndef BFQ_MULTI_EDGE_GROUPS
+#define BFQ_MULTI_EDGE_GROUPS 2
 #endif
 
 namespace bfq {
 namespace {
 
 constexpr int kCounterStride = 8;   // one 32-byte sector per query counter
+constexpr int kMultiGroups = BFQ_MULTI_EDGE_GROUPS;
 
 // Where the per-query state lives.
 struct MultiEnv {
@@ -56,50 +62,63 @@ __device__ __forceinline__ bool flush_multi(const MultiEnv& e, int home, unsigne
   return ok;
 }
 
+// A mixed batch staged for the merged edge walk (as BatchStage, with the
+// per-query fields): slot r holds the item of the r-th lane with edges.
+struct MultiStage {
+  long long ebase[32];          // address of merged-list position 0 for this item
+  long long* lbase[32];         // the item's query's labels
+  long long key0[32];           // (dist, hops + 1) of the tail's label
+  int q[32];                    // query
+  int vq[32];                   // the query graph's vertex count
+  int tail[32];
+};
+
 // Merged relaxation of a mixed batch: lane j owns edges [0, deg_j) at eptr_j
 // of a tail with label lab_j in query q_j, whose labels start at lbase_j in
-// the pool and which has V_j vertices.  MIN: one atomicMin per edge lowers
-// the label and claims the in-queue flag (keys are even, so key | 1 is below
-// a label exactly when key is below its key part); for labels that stay in
-// L2, since every atomic dirties its line.  Otherwise load, then
-// compare-and-swap when lower.
+// the pool and which has V_j vertices.  The items with edges are staged in
+// shared memory and each edge position finds its item's slot with
+// staged_owner.  MIN: one atomicMin per edge lowers the label and claims the
+// in-queue flag (keys are even, so key | 1 is below a label exactly when key
+// is below its key part); for labels that stay in L2, since every atomic
+// dirties its line.  Otherwise load, then compare-and-swap when lower.
 template <int U, bool MIN>
 __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2* eptr, int deg,
                                             long long lab, long long* lbase, int Vq, int q,
                                             int tail, int lane, int home, WarpCounters& wc,
                                             unsigned* buf, unsigned short* bufq, int& nbuf,
-                                            unsigned& walk_at) {
+                                            unsigned& walk_at, MultiStage* st) {
+  const bool has = lane < n && deg > 0;
+  const unsigned hm = __ballot_sync(kFullMask, has);
+  if (!hm) return true;
   int total = 0;
-  const int excl = warp_excl_scan(deg, lane, &total);
+  const int excl = warp_excl_scan(has ? deg : 0, lane, &total);
   wc.rel += (lane == 0) ? (unsigned)total : 0u;
+  if (has) {
+    const int r = __popc(hm & lanemask_lt());
+    st->ebase[r] = (long long)(size_t)eptr - (long long)sizeof(int2) * excl;
+    st->lbase[r] = lbase;
+    st->key0[r] = pack_label(label_dist(lab), label_hops(lab) + 1u);
+    st->q[r] = q;
+    st->vq[r] = Vq;
+    st->tail[r] = tail;
+  }
+  __syncwarp();
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
-    long long lab_t[U];
-    long long* lb[U];
-    int qq[U], vv[U], tl[U];
+    int own[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
       act[g] = false;
       cw[g] = make_int2(0, 0);
-      lab_t[g] = 0;
-      lb[g] = nullptr;
-      qq[g] = 0;
-      vv[g] = 0;
-      tl[g] = 0;
-      if (base + 32 * g < total) {          // warp-uniform
-        const int t = base + 32 * g + lane;
-        const int j = owner_lane(excl, t, n);
-        const int ex_j = __shfl_sync(kFullMask, excl, j);
-        const int2* ep = (const int2*)__shfl_sync(kFullMask, (unsigned long long)eptr, j);
-        lb[g] = (long long*)__shfl_sync(kFullMask, (unsigned long long)lbase, j);
-        lab_t[g] = __shfl_sync(kFullMask, lab, j);
-        qq[g] = __shfl_sync(kFullMask, q, j);
-        vv[g] = __shfl_sync(kFullMask, Vq, j);
-        tl[g] = __shfl_sync(kFullMask, tail, j);
-        if (t < total) {
+      own[g] = 0;
+      const int P = base + 32 * g;
+      if (P < total) {                      // warp-uniform
+        own[g] = staged_owner(has, excl, P);
+        if (P + lane < total) {
           act[g] = true;
-          cw[g] = __ldg(ep + (t - ex_j));
+          cw[g] = __ldg((const int2*)(size_t)(st->ebase[own[g]] +
+                                               (long long)sizeof(int2) * (P + lane)));
         }
       }
     }
@@ -109,16 +128,10 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
       key[g] = 0;
       cur[g] = 0;
       if (act[g]) {
-        const long long nd = (long long)label_dist(lab_t[g]) + (long long)cw[g].y;
-        if (nd >= (long long)kInf32) {
-          act[g] = false;
-        } else if (nd <= -2147483648LL) {
-          atomicOr(&e.qstatus[qq[g]], kStRange);
-          act[g] = false;
-        } else {
-          key[g] = pack_label((int)nd, label_hops(lab_t[g]) + 1u);
-          if (!MIN) cur[g] = ld_relaxed_s64(lb[g] + cw[g].x);
-        }
+        const int c = edge_candidate(st->key0[own[g]], cw[g].y, &key[g]);
+        if (c < 0) atomicOr(&e.qstatus[st->q[own[g]]], kStRange);
+        act[g] = c > 0;
+        if (act[g] && !MIN) cur[g] = ld_relaxed_s64(st->lbase[own[g]] + cw[g].x);
       }
     }
     long long prev[U];
@@ -126,7 +139,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
 #pragma unroll
       for (int g = 0; g < U; ++g) {
         prev[g] = 0;
-        if (act[g]) cur[g] = atomicMin(lb[g] + cw[g].x, key[g] | kQueuedBit);
+        if (act[g]) cur[g] = atomicMin(st->lbase[own[g]] + cw[g].x, key[g] | kQueuedBit);
       }
     } else {
       // first compare-and-swap of every group back to back (they overlap);
@@ -135,7 +148,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
       for (int g = 0; g < U; ++g) {
         prev[g] = cur[g];
         if (act[g] && key[g] < label_key(cur[g]))
-          prev[g] = (long long)atomicCAS((unsigned long long*)(lb[g] + cw[g].x),
+          prev[g] = (long long)atomicCAS((unsigned long long*)(st->lbase[own[g]] + cw[g].x),
                                          (unsigned long long)cur[g],
                                          (unsigned long long)(key[g] | kQueuedBit));
         else
@@ -147,24 +160,26 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
     for (int g = 0; g < U; ++g) {
       enq[g] = false;
       if (act[g]) {
+        long long* lb = st->lbase[own[g]];
         const int r =
             MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
                 : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
-                                      : lower_label(lb[g] + cw[g].x, key[g], prev[g]);
+                                      : lower_label(lb + cw[g].x, key[g], prev[g]);
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
-          if (nh >= (unsigned)vv[g]) {
-            atomicOr(&e.qstatus[qq[g]], kStNegCycle);
+          const int vq = st->vq[own[g]];
+          if (nh >= (unsigned)vq) {
+            atomicOr(&e.qstatus[st->q[own[g]]], kStNegCycle);
           } else {
             enq[g] = (r == 2);
             if (e.cyc && nh >= (e.cyc_walk0 >> 1)) {
-              long long* cb = e.cyc + (lb[g] - e.pool);
+              long long* cb = e.cyc + (lb - e.pool);
               st_relaxed_u64((unsigned long long*)(cb + cw[g].x),
-                             (unsigned long long)pack_edge(tl[g], cw[g].y));
+                             (unsigned long long)pack_edge(st->tail[own[g]], cw[g].y));
               if (nh >= walk_at) {
-                if (prove_negative_cycle(cb, lb[g], cw[g].x, vv[g]))
-                  atomicOr(&e.qstatus[qq[g]], kStNegCycle);
+                if (prove_negative_cycle(cb, lb, cw[g].x, vq))
+                  atomicOr(&e.qstatus[st->q[own[g]]], kStNegCycle);
                 else
                   walk_at = nh * 2;
               }
@@ -181,14 +196,15 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
           if (!flush_multi(e, home, buf, bufq, nbuf, lane, wc)) return false;
         }
         if (enq[g]) {
-          const int slot = nbuf + __popc(m & ((1u << lane) - 1u));
-          buf[slot] = (unsigned)((lb[g] - e.pool) + cw[g].x);
-          bufq[slot] = (unsigned short)qq[g];
+          const int slot = nbuf + __popc(m & lanemask_lt());
+          buf[slot] = (unsigned)((st->lbase[own[g]] - e.pool) + cw[g].x);
+          bufq[slot] = (unsigned short)st->q[own[g]];
         }
         nbuf += __popc(m);
       }
     }
   }
+  __syncwarp();                         // stage free for the next batch
   return true;
 }
 
