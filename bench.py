@@ -64,6 +64,9 @@ def parse_args(argv=None):
     p.add_argument("--no-forms", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default run-time parameters (profiling runs)")
+    p.add_argument("--tune", default="",
+                   help="fixed run-time parameters of the main line instead of the autotuner, "
+                        "e.g. share_div=1,l2_persist_pct=75 (profiling runs)")
     p.add_argument("--serve-requests", type=int, default=2000,
                    help="requests per arrival rate in the serving leg")
     return p.parse_args(argv)
@@ -347,11 +350,15 @@ def _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_
             raise RuntimeError(f"serve: request {rid} stuck; server state "
                                f"{bfq.bfq_server_state(sv)}") from e
 
+    # one request sequence (graph uniform over the mix, source uniform over
+    # its sources) for every rate, so that the rates differ only in their
+    # arrival times; each rate draws its own Poisson gaps
+    seq_g = rng.integers(0, len(all_g), size=n_req)
+    seq_s = [int(srcs[g][rng.integers(0, len(srcs[g]))]) for g in seq_g]
+
     def schedule(rate):
         gaps = rng.exponential(1.0 / rate, size=n_req)
-        gi = rng.integers(0, len(all_g), size=n_req)
-        si = [int(srcs[g][rng.integers(0, len(srcs[g]))]) for g in gi]
-        return np.cumsum(gaps), gi, si
+        return np.cumsum(gaps), seq_g, seq_s
 
     def run_server(times, gi, si):
         owner = [[None] * ring for _ in all_g]
@@ -412,6 +419,7 @@ def _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_
     stats = bfq.bfq_server_stats(sv)
     return {"workload": "serve: batched mix + R-MAT 23 (V=8,388,608), Poisson arrivals",
             "requests_per_rate": n_req, "batched_saturation_qps": sat_qps,
+            "large_requests_per_rate": int(np.sum(seq_g == len(all_g) - 1)),
             "burst_qps": burst_qps, "rates": rates, "server": stats,
             "budget_bytes": budget, "slots": 512,
             "latency": "host steady clock, submission to completion observed by the server"}
@@ -476,16 +484,18 @@ def queue_leg(dev, n_ops=10_000_000):
     if peaks["same_address_warp_cas"] > 0 and "enqdeq" in res.get("bq_warp", {}):
         frac["bq_warp"] = res["bq_warp"]["enqdeq"]["ops_per_s"] / peaks["same_address_warp_cas"]
     if peaks["same_address_ticket_add"] > 0 and "enqdeq" in res.get("bwd_warp", {}):
-        # two one-address atomics (reservation, ticket) per 32 operations
+        # two one-address reservations (count, ticket) per operation, as for
+        # the per-thread queues whose same-address adds the hardware
+        # aggregates per warp; the warp form makes that aggregation explicit
         frac["bwd_warp"] = (res["bwd_warp"]["enqdeq"]["ops_per_s"] /
-                            (16.0 * peaks["same_address_ticket_add"]))
+                            (0.5 * peaks["same_address_ticket_add"]))
     return {"ops": n_ops, "variants": res, "atomic_peaks_ops_per_s": peaks,
             "enqdeq_frac_of_atomic_peak": frac,
             "note": "EnqDeq counts n enqueues + n dequeues; Mixed counts n/2 + n/2 attempts; "
                     "per-thread BQ/BWD against one-address ticket adds, the exact-count "
                     "warp queue against one-address warp compare-and-swap, the single-shot "
-                    "warp queue against 16 x one-address ticket adds (two atomics per "
-                    "32 operations)"}
+                    "warp queue against half the one-address ticket-add rate (two "
+                    "reservations per operation)"}
 
 
 def rounds_leg(h, srcs, dist_t, flush, stream, m_per_query, queue_kernel_ms):
@@ -763,8 +773,17 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # run-time parameters picked by the library's autotuner (untimed)
-    tuned = bfq.bfq_graph_get_tune(h) if args.no_autotune else bfq.bfq_autotune(h, srcs)
+    # run-time parameters picked by the library's autotuner (untimed), or
+    # fixed ones given on the command line
+    if args.tune:
+        t = bfq.bfq_graph_get_tune(h)
+        for kv in args.tune.split(","):
+            k, v = kv.split("=")
+            setattr(t, k.strip(), int(v))
+        bfq.bfq_graph_set_tune(h, t)
+        tuned = bfq.bfq_graph_get_tune(h)
+    else:
+        tuned = bfq.bfq_graph_get_tune(h) if args.no_autotune else bfq.bfq_autotune(h, srcs)
     tune_desc = {"share_div": tuned.share_div, "chunk_batch": tuned.chunk_batch,
                  "batch_items": tuned.batch_items,
                  "kernel_ctas": tuned.kernel_ctas or ("3 (auto)" if g.E < 8 * V else "4 (auto)"),

@@ -45,7 +45,8 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 // edges [beg_j, beg_j + deg_j) of a tail whose label is lab_j.  The items
 // with edges are staged in shared memory (BatchStage) and the edges walked
 // lane-contiguously, U groups of 32 per step so that the loads of the
-// groups overlap.  Returns false on a timeout.
+// groups overlap; the next step's edge loads are issued before this step's
+// label atomics, so the two round trips overlap.  Returns false on a timeout.
 // Claimed children are appended to the warp's buffer `buf` (nbuf items,
 // capacity kChildBuf) and published in bulk by flush_children.
 template <int U, bool MIN>
@@ -67,21 +68,39 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
   }
   __syncwarp();
   const unsigned V = (unsigned)a.V;
+  int2 nx_cw[U];
+  int nx_own[U];
+  bool nx_act[U];
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    nx_act[g] = false;
+    nx_cw[g] = make_int2(0, 0);
+    nx_own[g] = 0;
+    const int P = 32 * g;
+    if (P < total) {
+      nx_own[g] = staged_owner(has, excl, P);
+      if (P + lane < total) {
+        nx_act[g] = true;
+        nx_cw[g] = __ldg(&a.adj[st->off[nx_own[g]] + P + lane]);
+      }
+    }
+  }
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
     int own[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
-      act[g] = false;
-      cw[g] = make_int2(0, 0);
-      own[g] = 0;
-      const int P = base + 32 * g;
+      cw[g] = nx_cw[g];
+      own[g] = nx_own[g];
+      act[g] = nx_act[g];
+      nx_act[g] = false;
+      const int P = base + 32 * U + 32 * g;
       if (P < total) {                      // warp-uniform
-        own[g] = staged_owner(has, excl, P);
+        nx_own[g] = staged_owner(has, excl, P);
         if (P + lane < total) {
-          act[g] = true;
-          cw[g] = __ldg(&a.adj[st->off[own[g]] + P + lane]);
+          nx_act[g] = true;
+          nx_cw[g] = __ldg(&a.adj[st->off[nx_own[g]] + P + lane]);
         }
       }
     }

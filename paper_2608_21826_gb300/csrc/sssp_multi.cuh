@@ -77,7 +77,8 @@ struct MultiStage {
 // of a tail with label lab_j in query q_j, whose labels start at lbase_j in
 // the pool and which has V_j vertices.  The items with edges are staged in
 // shared memory and each edge position finds its item's slot with
-// staged_owner.  MIN: one atomicMin per edge lowers the label and claims the
+// staged_owner; the next step's edge loads are issued before this step's
+// label atomics.  MIN: one atomicMin per edge lowers the label and claims the
 // in-queue flag (keys are even, so key | 1 is below a label exactly when key
 // is below its key part); for labels that stay in L2, since every atomic
 // dirties its line.  Otherwise load, then compare-and-swap when lower.
@@ -103,22 +104,41 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
     st->tail[r] = tail;
   }
   __syncwarp();
+  int2 nx_cw[U];
+  int nx_own[U];
+  bool nx_act[U];
+#pragma unroll
+  for (int g = 0; g < U; ++g) {
+    nx_act[g] = false;
+    nx_cw[g] = make_int2(0, 0);
+    nx_own[g] = 0;
+    const int P = 32 * g;
+    if (P < total) {
+      nx_own[g] = staged_owner(has, excl, P);
+      if (P + lane < total) {
+        nx_act[g] = true;
+        nx_cw[g] = __ldg((const int2*)(size_t)(st->ebase[nx_own[g]] +
+                                                (long long)sizeof(int2) * (P + lane)));
+      }
+    }
+  }
   for (int base = 0; base < total; base += 32 * U) {
     int2 cw[U];
     int own[U];
     bool act[U];
 #pragma unroll
     for (int g = 0; g < U; ++g) {
-      act[g] = false;
-      cw[g] = make_int2(0, 0);
-      own[g] = 0;
-      const int P = base + 32 * g;
+      cw[g] = nx_cw[g];
+      own[g] = nx_own[g];
+      act[g] = nx_act[g];
+      nx_act[g] = false;
+      const int P = base + 32 * U + 32 * g;
       if (P < total) {                      // warp-uniform
-        own[g] = staged_owner(has, excl, P);
+        nx_own[g] = staged_owner(has, excl, P);
         if (P + lane < total) {
-          act[g] = true;
-          cw[g] = __ldg((const int2*)(size_t)(st->ebase[own[g]] +
-                                               (long long)sizeof(int2) * (P + lane)));
+          nx_act[g] = true;
+          nx_cw[g] = __ldg((const int2*)(size_t)(st->ebase[nx_own[g]] +
+                                                  (long long)sizeof(int2) * (P + lane)));
         }
       }
     }
