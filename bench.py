@@ -687,6 +687,27 @@ def grid_leg(dev, reps=5):
                            reps)
 
 
+def relax_pattern_leg(dev, n_edges, n_labels, reps=3):
+    """The relaxation step's memory pattern alone on this GPU (no queues):
+    as many edges as one query relaxes, read lane-contiguously, each with one
+    random 64-bit atomicMin into a label array of the workload's size.  Its
+    edges per second are the measured bound of the relax phase."""
+    import torch
+    from paper_2608_21826_gb300 import bfq
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    best = None
+    for _ in range(reps):
+        ms, low = bfq.bfq_relax_bench(int(n_edges), int(n_labels), sms * 8, 256)
+        if best is None or ms < best[0]:
+            best = (ms, low)
+    ms, low = best
+    return {"edges": int(n_edges), "labels": int(n_labels), "ms": ms,
+            "edges_per_s": n_edges / (ms / 1e3), "lowered": low,
+            "bytes_per_s": 16.0 * n_edges / (ms / 1e3),
+            "note": "8 B (col, w) read + one 8 B atomicMin per edge, best of "
+                    f"{reps}; grid = SMs x 8 CTAs of 256"}
+
+
 def worklist_forms_leg(h, srcs, dist_t, flush, stream, reps=3):
     """The two reservation forms of the worklist's sub-queues on the same
     handle and sources, at the handle's other tuned parameters: exact-count
@@ -860,7 +881,12 @@ def run_ours(args):
     # clocks seen over both timed regions (device-timed and end to end)
     clk = clocks.stop()
 
-    rounds = l2 = forms = None
+    rounds = l2 = forms = relax_pat = None
+    if rank == 0:
+        try:
+            relax_pat = relax_pattern_leg(dev, rel / n_q, V)
+        except Exception as e:                               # reported, not fatal
+            relax_pat = {"error": repr(e)}
     if rank == 0 and not args.no_forms:
         try:
             forms = worklist_forms_leg(h, srcs, dist_t, flush, stream)
@@ -941,7 +967,12 @@ def run_ours(args):
                  "work_gteps": rel / t_dev / 1e9,
                  # the same roofline counting each reached edge once (no
                  # re-relaxation): the useful share of the bytes moved
-                 "useful_frac": (4.0 * V * n_q + 20.0 * deq + 12.0 * m_reached) / k_s / 1e9 / peak},
+                 "useful_frac": (4.0 * V * n_q + 20.0 * deq + 12.0 * m_reached) / k_s / 1e9 / peak,
+                 # edges relaxed per second of kernel time against the same
+                 # memory pattern run alone (no queues): the relax phase's bound
+                 "frac_of_relax_pattern": ((rel / k_s) / relax_pat["edges_per_s"]
+                                           if relax_pat and "edges_per_s" in relax_pat else None)},
+        "relax_pattern": relax_pat,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 3 * n_q,

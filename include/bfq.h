@@ -438,6 +438,18 @@ int bfq_queue_mixed(bfq_queue_t q, const int32_t* items, int64_t n_enq,
 int bfq_atomic_bench(int32_t mode, int64_t n_ops, int32_t grid, int32_t block,
                      double* ms_out, int64_t* total_out, void* stream);
 
+/* The relaxation step's memory pattern alone, as the measured bound of the
+ * SSSP kernels' relax phase (the paper has no counterpart): n_edges (col, w)
+ * pairs, generated on the device, are read lane-contiguously (8 B per edge,
+ * two per lane in flight) and each applies one 64-bit atomicMin to a random
+ * one of n_labels labels, with no queue work.  grid x block threads; *ms_out
+ * (nullable) receives the CUDA-event time of the relax launch (generation
+ * untimed) and *lowered_out (nullable) the number of atomics that lowered a
+ * label.  Allocates 8 B per edge and per label for the call; synchronises
+ * `stream`. */
+int bfq_relax_bench(int64_t n_edges, int32_t n_labels, int32_t grid, int32_t block,
+                    double* ms_out, int64_t* lowered_out, void* stream);
+
 /* Read head, tail and count (host pointers, each nullable) and the queue's
  * error word; synchronises `stream`.  Returns BFQ_OK or BFQ_ERR_TIMEOUT if a
  * ticket wait of an earlier launch ran out. */

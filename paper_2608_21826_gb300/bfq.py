@@ -113,6 +113,8 @@ _SIGNATURES = {
                          ctypes.POINTER(_I64), _VP], ctypes.c_int),
     "bfq_atomic_bench": ([_I32, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(_I64), _VP], ctypes.c_int),
+    "bfq_relax_bench": ([_I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(_I64), _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -476,6 +478,14 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def bfq_relax_bench(n_edges: int, n_labels: int, grid: int, block: int, stream=None):
+    """Relaxation memory pattern alone; returns (ms, lowered)."""
+    ms, low = ctypes.c_double(), _I64()
+    _check(lib().bfq_relax_bench(int(n_edges), int(n_labels), int(grid), int(block),
+                                 ctypes.byref(ms), ctypes.byref(low), _stream(stream)))
+    return ms.value, low.value
 
 
 def bfq_atomic_bench(mode: int, n_ops: int, grid: int, block: int, stream=None):

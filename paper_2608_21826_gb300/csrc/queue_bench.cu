@@ -269,9 +269,90 @@ __global__ void atomic_bench_kernel(unsigned long long* ctr, long long n_ops, in
   if (acc == 0x5eed5eed5eed5eedull) *sink = acc;   // keeps the results live
 }
 
+// The relaxation step's memory pattern alone (no queues, no decisions): a
+// stream of (col, w) pairs read lane-contiguously, 8 bytes per edge, and one
+// 64-bit atomicMin per edge at label[col], two edges per lane in flight as in
+// the SSSP kernel's merged walk.  The number of labels the atomics lowered is
+// summed into *lowered.
+__global__ void relax_bench_fill_kernel(int2* edges, long long n_edges, int n_labels,
+                                        long long* label) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < n_edges; i += nth) {
+    unsigned long long h = (unsigned long long)i * 0x9e3779b97f4a7c15ull;
+    h ^= h >> 29;
+    h *= 0xbf58476d1ce4e5b9ull;
+    h ^= h >> 32;
+    edges[i] = make_int2((int)(h % (unsigned long long)n_labels), (int)((h >> 40) & 255u));
+  }
+  for (long long v = tid; v < n_labels; v += nth) label[v] = kInfLabel;
+}
+
+__global__ void relax_bench_kernel(const int2* __restrict__ edges, long long n_edges,
+                                   long long* label, unsigned long long* lowered) {
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long low = 0;
+  const long long base_key = pack_label(1000, 1);
+  for (long long i = tid; i < n_edges; i += 2 * nth) {
+    const int2 e0 = __ldg(&edges[i]);
+    const bool two = i + nth < n_edges;
+    const int2 e1 = two ? __ldg(&edges[i + nth]) : make_int2(0, 0);
+    const long long k0 = base_key + (long long)((unsigned long long)(long long)e0.y << 32);
+    const long long k1 = base_key + (long long)((unsigned long long)(long long)e1.y << 32);
+    const long long o0 = atomicMin(&label[e0.x], k0 | kQueuedBit);
+    const long long o1 = two ? atomicMin(&label[e1.x], k1 | kQueuedBit) : k1;
+    low += (k0 < label_key(o0)) + (two && k1 < label_key(o1));
+  }
+  low = __reduce_add_sync(kFullMask, (unsigned)low);
+  if ((threadIdx.x & 31) == 0) atomicAdd(lowered, low);
+}
+
 extern "C" {
 
 static int check_launch(int32_t grid, int32_t block, int64_t n);
+
+int bfq_relax_bench(int64_t n_edges, int32_t n_labels, int32_t grid, int32_t block,
+                    double* ms_out, int64_t* lowered_out, void* stream) {
+  if (n_edges < 1 || n_labels < 1) return q_invalid("bfq_relax_bench: n_edges and n_labels must be >= 1");
+  int rc = check_launch(grid, block, n_edges);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int2* edges = nullptr;
+  long long* label = nullptr;
+  unsigned long long* low = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&edges, sizeof(int2) * (size_t)n_edges);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&label, sizeof(long long) * (size_t)n_labels);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&low, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(low, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    relax_bench_fill_kernel<<<2048, 256, 0, s>>>(edges, n_edges, n_labels, label);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) {
+    relax_bench_kernel<<<grid, block, 0, s>>>(edges, n_edges, label, low);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  unsigned long long lowered = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&lowered, low, sizeof(lowered), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(edges);
+  cudaFree(label);
+  cudaFree(low);
+  if (e != cudaSuccess) return cuda_fail(e, "bfq_relax_bench", __FILE__, __LINE__);
+  if (ms_out) *ms_out = ms;
+  if (lowered_out) *lowered_out = (int64_t)lowered;
+  return BFQ_OK;
+}
 
 int bfq_atomic_bench(int32_t mode, int64_t n_ops, int32_t grid, int32_t block,
                      double* ms_out, int64_t* total_out, void* stream) {

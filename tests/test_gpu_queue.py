@@ -135,3 +135,14 @@ def test_atomic_bench_rejects_bad_arguments():
     for args in ((3, 1024, 8, 64), (0, 1024, 8, 48), (2, 1000, 8, 64), (0, -1, 8, 64)):
         with pytest.raises(bfq.BfqError):
             bfq.bfq_atomic_bench(*args)
+
+
+def test_relax_bench_runs_and_counts():
+    """The relaxation-pattern microbenchmark touches every edge once: with
+    labels starting at infinity, at least one atomic per distinct label
+    lowers it, and no more atomics than edges do."""
+    n, L = 1 << 20, 1 << 16
+    ms, low = bfq.bfq_relax_bench(n, L, 152 * 4, 256)
+    assert ms > 0 and L // 2 <= low <= n
+    with pytest.raises(bfq.BfqError):
+        bfq.bfq_relax_bench(0, L, 8, 64)
