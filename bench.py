@@ -318,7 +318,18 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7, tune=None):
     g23 = synth.workload_rmat(23)
     h23 = bfq.bfq_graph_create(g23.row_ptr, g23.col, g23.w)
     # large requests run alone on this handle: tune it (untimed)
-    bfq.bfq_autotune(h23, [int(x) for x in g23.sources])
+    t23 = bfq.bfq_autotune(h23, [int(x) for x in g23.sources])
+    d23 = torch.empty(g23.V, dtype=torch.int32, device=dev)
+    k23 = []
+    for _ in range(2):
+        for x in g23.sources:
+            bfq.bfq_sssp(h23, int(x), d23)
+            k23.append(bfq.bfq_get_stats(h23)["kernel_ms"])
+    large = {"tune": {f: getattr(t23, f) for f in ("share_div", "chunk_batch", "batch_items",
+                                                     "kernel_ctas", "queue_form", "relax_atomic",
+                                                     "l2_persist_pct")},
+             "kernel_ms_per_query": sum(k23) / len(k23)}
+    del d23
     all_g = list(graphs) + [g23]
     all_h = list(handles) + [h23]
     rng = np.random.default_rng(seed)
@@ -334,6 +345,7 @@ def serve_leg(dev, graphs, handles, sat_qps, n_req, seed=7, tune=None):
         out = _serve_runs(sv, bfq, torch, dev, all_g, all_h, bufs, ring, budget, rng, sat_qps,
                           n_req)
         out["tune"] = tune
+        out["large_graph"] = large
         return out
     finally:
         bfq.bfq_server_destroy(sv)

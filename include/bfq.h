@@ -313,10 +313,10 @@ int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
  * and copy them to *out (nullable).  Times a fixed grid of candidates in the
  * handle's register form over one pass of the sources each, the best four
  * again over four passes, then, one at a time at the best so far, the other
- * register form, the other queue form, the other relaxation form and an L2
- * set-aside of 50 and 75 percent for the labels (CUDA events, each pass
- * after an untimed one); allocates one int32[V] scratch array for the
- * duration.  Synchronises `stream`. */
+ * register form, the other queue form, the other relaxation form, and an L2
+ * set-aside of 50 and 75 percent for the labels with either relaxation form
+ * (CUDA events, each pass after an untimed one); allocates one int32[V]
+ * scratch array for the duration.  Synchronises `stream`. */
 int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
 
 /* ---- batched queries: many sources over many resident graphs in one

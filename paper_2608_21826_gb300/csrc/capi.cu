@@ -629,12 +629,21 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
     cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
     cudaGetLastError();
     if (max_persist > 0) {
+      // with either relaxation form: a set-aside that keeps the labels from
+      // being evicted by the adjacency stream can make atomicMin pay where
+      // it lost without one (labels near half of L2)
       const bfq_tune base = best_t;
-      for (int pct : {50, 75}) {
-        bfq_tune c = base;
-        c.l2_persist_pct = pct;
-        try_one(c);
-      }
+      const bool base_min =
+          base.relax_atomic == BFQ_RELAX_MIN ||
+          (base.relax_atomic == BFQ_RELAX_AUTO &&
+           (long long)sizeof(long long) * g->V <= g->l2_bytes / 2);
+      for (int pct : {50, 75})
+        for (int other = 0; other < 2; ++other) {
+          bfq_tune c = base;
+          c.l2_persist_pct = pct;
+          if (other) c.relax_atomic = base_min ? BFQ_RELAX_CAS : BFQ_RELAX_MIN;
+          try_one(c);
+        }
     }
   }
   cudaStreamSynchronize(s);
