@@ -302,7 +302,11 @@ int bfq_sssp_rounds(bfq_graph_t g, int32_t src, int32_t flags, int32_t* dist,
  * the label array to the persistent launch.  Setting it back to 0, or
  * destroying the handle, drops the persisting lines and restores the
  * context's previous persisting-L2 limit (the set-aside takes L2 capacity
- * from every other kernel of the process while it is held). */
+ * from every other kernel of the process while it is held).  With a non-zero
+ * share, bfq_sssp (the synchronous call) turns the persisting lines back into
+ * normal ones once its query is over (cudaCtxResetPersistingL2Cache, which
+ * acts on the whole context); bfq_sssp_async leaves them, so that queries in
+ * a row on one handle keep their labels in L2. */
 int bfq_graph_get_tune(bfq_graph_t g, bfq_tune* out);
 int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
 

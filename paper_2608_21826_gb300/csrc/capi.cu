@@ -453,6 +453,9 @@ int bfq_sssp(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* 
   BFQ_CUDA_TRY(cudaMemcpyAsync(g->status_host, g->status_dev, sizeof(int32_t),
                                cudaMemcpyDeviceToHost, s));
   BFQ_CUDA_TRY(cudaStreamSynchronize(s));
+  // the query is over: turn its persisting lines back into normal ones, so
+  // that the set-aside holds no stale labels for other work
+  if (g->l2_pct_applied > 0) cudaCtxResetPersistingL2Cache();
   const int st = *g->status_host;
   if (st == BFQ_ERR_TIMEOUT) set_error("bfq_sssp: a bounded device-side wait ran out");
   return st;

@@ -958,6 +958,13 @@ struct bfq_server {
       if (solo_state == 2) {
         const cudaError_t se = cudaEventQuery(solo_done);
         if (se != cudaErrorNotReady) {
+          // nothing else runs now: persisting lines the large query's L2
+          // window left behind become normal lines again before the
+          // resident kernel resumes
+          int lpct = 0;
+          bfq_tune lt{};
+          if (bfq_graph_get_tune(graphs[solo_rq.graph], &lt) == BFQ_OK) lpct = lt.l2_persist_pct;
+          if (lpct > 0) cudaCtxResetPersistingL2Cache();
           auto rec = records.find(solo_rq.id);
           if (rec != records.end()) {
             rec->second.status = se == cudaSuccess ? *solo_status : BFQ_ERR_CUDA;
