@@ -139,21 +139,24 @@ __device__ __forceinline__ long long label_key(long long l) { return l & ~kQueue
 // ---------------------------------------------------------------------------
 // warp-aggregated Broker Queue (sub-queue of the SSSP worklist)
 // ---------------------------------------------------------------------------
-// One sub-queue's counters, each in its own 32-byte L2 sector.
+// One sub-queue's counters, each on its own 128-byte line.  Within one line
+// the atomics of the four counters serialise (the single-shot warp queue ran
+// at 11.2 G ops/s with its counters 32 bytes apart, 21.1 G with them on
+// separate lines; the counters of a line most likely share one L2 slice).
 struct alignas(128) QueueMeta {
   int count;                    // exact form: broker count, items granted and
                                 //   not yet taken; single-shot form: items
                                 //   published and not yet granted to dequeuers
-  int pad0[7];
+  int pad0[31];
   unsigned long long head;      // dequeue ticket counter
-  unsigned long long pad1[3];
+  unsigned long long pad1[15];
   unsigned long long tail;      // enqueue ticket counter
-  unsigned long long pad2[3];
+  unsigned long long pad2[15];
   int used;                     // single-shot form: places granted to
                                 //   enqueuers and not yet released by dequeuers
-  int pad3[7];
+  int pad3[31];
 };
-static_assert(sizeof(QueueMeta) == 128, "QueueMeta layout");
+static_assert(sizeof(QueueMeta) == 512, "QueueMeta layout");
 
 // Slot word: (ticket << 32) | item.  Ticket 2*lap means "free for the
 // enqueuer of lap `lap`", 2*lap+1 "holds the item of lap `lap`"; packing the
