@@ -20,7 +20,8 @@
 namespace bfq {
 namespace {
 
-constexpr int kCounterStride = 8;   // one 32-byte sector per query counter
+constexpr int kCounterStride = 32;  // one 128-byte line per query counter (4 per line
+                                     // serialise: batched mix 34.8 against 32.9 ms)
 constexpr int kMultiGroups = BFQ_MULTI_EDGE_GROUPS;
 
 // Where the per-query state lives.
