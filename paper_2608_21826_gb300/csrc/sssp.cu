@@ -24,13 +24,20 @@ namespace bfq {
 namespace {
 
 // Count the buffered children as in flight (before any becomes visible),
-// then publish them.
+// then publish them.  retire (> 0 only once the warp's batch is fully
+// relaxed) is the batch's item count, taken off in the same update: the
+// single in-flight counter is the kernel's most contended address, so a
+// batch changes it once, not twice.
 __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsigned* buf,
-                                               int& nbuf, int lane, WarpCounters& wc) {
-  if (nbuf == 0) return true;
+                                               int& nbuf, int lane, WarpCounters& wc,
+                                               int retire = 0) {
+  if (nbuf == 0) {
+    if (retire && lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -retire);
+    return true;
+  }
   __syncwarp();                         // buffer writes visible to all lanes
   if (lane == 0) {
-    red_add_relaxed_s32(&a.ctl->inflight, nbuf);
+    red_add_relaxed_s32(&a.ctl->inflight, nbuf - retire);
     wc.enq += nbuf;
   }
   __syncwarp();
@@ -368,16 +375,16 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
         break;
       }
     }
+    // relax, then publish the children and retire the batch in one update
+    // of the in-flight count: its children are counted before any becomes
+    // visible, and the batch is done with; the labels are read by the
+    // epilogue kernel, after this kernel has ended.
     if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
                                     walk_at, st) ||
-        !flush_children(a, home, buf, nbuf, lane, wc)) {
+        !flush_children(a, home, buf, nbuf, lane, wc, got)) {
       timed_out = true;
       break;
     }
-    // retire the batch.  Its children were counted by this lane earlier, on
-    // the same counter, so coherence orders this decrement after them; the
-    // labels are read by the epilogue kernel, after this kernel has ended.
-    if (lane == 0) red_add_relaxed_s32(&a.ctl->inflight, -got);
   }
   if (timed_out && lane == 0) raise_status(a.ctl, kStTimeout);
 
