@@ -89,6 +89,17 @@ def test_random_with_cycles_cas_relaxation(seed):
     _compare(g, 0, gpu_util.sssp(g, 0, tune=t, want_pred=True), check_pred=True)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_random_with_cycles_single_shot_queues(seed):
+    """Minus-infinity marking with single-shot sub-queues (children published
+    in the same round trips as the next dequeue)."""
+    rng = np.random.default_rng(80 + seed)
+    V = int(rng.integers(100, 3000))
+    g = synth.random_graph(V, 5 * V, seed=950 + seed, wlo=-3, whi=40)
+    t = bfq.make_tune(neg_cycle_mode=bfq.NEG_CYCLE_MARK, queue_form=bfq.QUEUE_FORM_SINGLE_SHOT)
+    _compare(g, 0, gpu_util.sssp(g, 0, tune=t, want_pred=True), check_pred=True)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_planted_cycles_grid(seed):
     base = synth.grid_graph(64, 64, seed=seed)

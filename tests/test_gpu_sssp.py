@@ -395,3 +395,31 @@ def test_queue_forms_full_size_and_cycles(form):
             _compare(g, int(srcs[0]), gpu_util.run(h, g.V, int(srcs[0])))
         finally:
             bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_single_shot_random_and_edge_cases(seed):
+    """The single-shot sub-queues (whose warps publish a batch's children in
+    the same round trips as their next dequeue) on random graphs with and
+    without cycles, a hub star, a long path and the golden fixtures."""
+    rng = np.random.default_rng(300 + seed)
+    t = bfq.make_tune(queue_form=2)
+    V = int(rng.integers(1, 4000))
+    g = (synth.random_graph(V, int(rng.integers(0, 4 * V + 1)), seed=seed, wlo=-3, whi=40)
+         if seed % 2 else synth.random_potential_graph(max(2, V), 5 * max(2, V), seed=seed))
+    _compare(g, 0, gpu_util.sssp(g, 0, tune=t, want_pred=True), check_pred=True)
+    if seed == 0:
+        w = np.random.default_rng(1).integers(-1000, 1000, size=60_000 - 1).astype(np.int32)
+        star = synth.star_graph(60_000, w)
+        st, d, h, p = gpu_util.sssp(star, 0, tune=t, want_pred=True)
+        assert st == bfq.OK and np.array_equal(d[1:], w) and np.all(p[1:] == 0)
+        pw = np.random.default_rng(2).integers(-5, 9, size=5_000 - 1).astype(np.int32)
+        path = synth.path_graph(5_000, pw)
+        st, d, h, _ = gpu_util.sssp(path, 0, tune=t)
+        assert st == bfq.OK and np.array_equal(d, np.r_[0, np.cumsum(pw)])
+        for fx in helpers.golden_files():
+            gg, exp = helpers.load_golden(fx)
+            st, d, h, _ = gpu_util.sssp(gg, 0, tune=t)
+            assert st == exp["status"], fx
+            if "dist" in exp:
+                assert d.tolist() == exp["dist"] and h.tolist() == exp["hops"], fx
