@@ -118,10 +118,14 @@ typedef struct bfq_tune {
   int32_t relax_atomic;     /* how bfq_sssp lowers a label: BFQ_RELAX_AUTO,
                                BFQ_RELAX_MIN (one atomicMin per edge: fastest
                                while the label array sits in L2, but every
-                               atomic dirties its line) or BFQ_RELAX_CAS (load,
-                               then compare-and-swap only when lower).  AUTO
-                               takes MIN when 8 V <= half of L2.  Results are
-                               the same either way.                          */
+                               atomic dirties its line), BFQ_RELAX_FILTERED
+                               (load, then atomicMin only when lower: fewer
+                               atomics where most relaxations fail) or
+                               BFQ_RELAX_CAS (load, then compare-and-swap
+                               only when lower).  AUTO takes FILTERED when
+                               8 V <= half of L2 and E >= 8 V, MIN when
+                               8 V <= half of L2 otherwise, else CAS.
+                               Results are the same in every form.           */
   int32_t batch_budget_klabels; /* batched queries: labels (in units of 1024)
                                of the queries running at once.  Queries start
                                in order while the running ones fit, so their
@@ -169,6 +173,7 @@ typedef struct bfq_tune {
 #define BFQ_RELAX_AUTO 0
 #define BFQ_RELAX_MIN 1
 #define BFQ_RELAX_CAS 2
+#define BFQ_RELAX_FILTERED 3
 
 /* Counters of the last finished run on a graph handle (summed over warps). */
 typedef struct bfq_stats {
@@ -445,14 +450,17 @@ int bfq_atomic_bench(int32_t mode, int64_t n_ops, int32_t grid, int32_t block,
 /* The relaxation step's memory pattern alone, as the measured bound of the
  * SSSP kernels' relax phase (the paper has no counterpart): n_edges (col, w)
  * pairs, generated on the device, are read lane-contiguously (8 B per edge,
- * two per lane in flight) and each applies one 64-bit atomicMin to a random
- * one of n_labels labels, with no queue work.  grid x block threads; *ms_out
- * (nullable) receives the CUDA-event time of the relax launch (generation
- * untimed) and *lowered_out (nullable) the number of atomics that lowered a
- * label.  Allocates 8 B per edge and per label for the call; synchronises
- * `stream`. */
-int bfq_relax_bench(int64_t n_edges, int32_t n_labels, int32_t grid, int32_t block,
-                    double* ms_out, int64_t* lowered_out, void* stream);
+ * two per lane in flight) and each relaxes a random one of n_labels labels
+ * (starting at infinity) with a key of 256 possible distances, with no queue
+ * work.  mode 0: one 64-bit atomicMin per edge; 1: a load of the label, then
+ * the atomicMin only when the key is below it (the BFQ_RELAX_FILTERED form).
+ * grid x block threads; *ms_out (nullable) receives the CUDA-event time of
+ * the relax launch (generation untimed) and *lowered_out (nullable) the
+ * number of edges that lowered a label.  Allocates 8 B per edge and per
+ * label for the call; synchronises `stream`.  BFQ_ERR_INVALID for a mode
+ * other than 0 or 1, n_edges or n_labels < 1, or a bad launch shape. */
+int bfq_relax_bench(int32_t mode, int64_t n_edges, int32_t n_labels, int32_t grid,
+                    int32_t block, double* ms_out, int64_t* lowered_out, void* stream);
 
 /* Read head, tail and count (host pointers, each nullable) and the queue's
  * error word; synchronises `stream`.  Returns BFQ_OK or BFQ_ERR_TIMEOUT if a

@@ -61,7 +61,7 @@ class RoundsStats(ctypes.Structure):
 
 ROUNDS_ALL_EDGES = 1
 NEG_CYCLE_STOP, NEG_CYCLE_MARK = 0, 1
-RELAX_AUTO, RELAX_MIN, RELAX_CAS = 0, 1, 2
+RELAX_AUTO, RELAX_MIN, RELAX_CAS, RELAX_FILTERED = 0, 1, 2, 3
 NEG_INF = -2147483648          # dist of a vertex reachable from a negative cycle (MARK)
 
 _VP = ctypes.c_void_p
@@ -113,7 +113,7 @@ _SIGNATURES = {
                          ctypes.POINTER(_I64), _VP], ctypes.c_int),
     "bfq_atomic_bench": ([_I32, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(_I64), _VP], ctypes.c_int),
-    "bfq_relax_bench": ([_I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_double),
+    "bfq_relax_bench": ([_I32, _I64, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(_I64), _VP], ctypes.c_int),
 }
 
@@ -480,10 +480,12 @@ class Graph:
             pass
 
 
-def bfq_relax_bench(n_edges: int, n_labels: int, grid: int, block: int, stream=None):
-    """Relaxation memory pattern alone; returns (ms, lowered)."""
+def bfq_relax_bench(mode: int, n_edges: int, n_labels: int, grid: int, block: int,
+                    stream=None):
+    """Relaxation memory pattern alone (mode 0: atomicMin per edge, 1: load
+    then atomicMin when lower); returns (ms, lowered)."""
     ms, low = ctypes.c_double(), _I64()
-    _check(lib().bfq_relax_bench(int(n_edges), int(n_labels), int(grid), int(block),
+    _check(lib().bfq_relax_bench(int(mode), int(n_edges), int(n_labels), int(grid), int(block),
                                  ctypes.byref(ms), ctypes.byref(low), _stream(stream)))
     return ms.value, low.value
 

@@ -53,7 +53,7 @@ struct SsspArgs {
   int phantom;                  // test hook: unbacked in-flight items
   int mark_neg_inf;             // 1: resolve negative cycles to minus infinity
   unsigned cyc_walk0;           // first cycle-walk threshold (hops); records from half
-  int relax_min;                // 1: relax with one atomicMin (labels fit in L2)
+  int relax_min;                // 0: CAS, 1: one atomicMin, 2: load then atomicMin
   int wide;                     // 1: the 80-register build (3 CTAs per SM), else 64
   int q_alloc;                  // sub-queues allocated (qs.Q of them serve this run;
   int cq_alloc;                 //   a reset clears all); 0: as many as qs.Q / cq.Q

@@ -179,7 +179,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       out->share_div < 0 || out->chunk_batch < 1 || out->chunk_batch > 32 ||
       (out->neg_cycle_mode != BFQ_NEG_CYCLE_STOP && out->neg_cycle_mode != BFQ_NEG_CYCLE_MARK) ||
       out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30) ||
-      out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_CAS ||
+      out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_FILTERED ||
       (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4) ||
       out->queue_form < BFQ_QUEUE_FORM_AUTO || out->queue_form > BFQ_QUEUE_FORM_SINGLE_SHOT)
     return invalid("bfq_tune: bad limits");
@@ -344,6 +344,22 @@ static int wide_form(bfq_graph_t g, const bfq_tune& t) {
   return t.kernel_ctas == 3 ? 1 : t.kernel_ctas == 4 ? 0 : g->E < 8LL * g->V ? 1 : 0;
 }
 
+// Relaxation form of the persistent kernel (SsspArgs::relax_min: 0 CAS,
+// 1 atomicMin, 2 filtered atomicMin).  AUTO: atomicMin while the label array
+// fits in half of L2, filtered from an average out-degree of 8, where most
+// relaxations fail; compare-and-swap once the labels outgrow L2.
+static const int32_t kRelaxTuneOf[3] = {BFQ_RELAX_CAS, BFQ_RELAX_MIN, BFQ_RELAX_FILTERED};
+static int relax_form(bfq_graph_t g, int32_t relax_atomic) {
+  switch (relax_atomic) {
+    case BFQ_RELAX_CAS: return 0;
+    case BFQ_RELAX_MIN: return 1;
+    case BFQ_RELAX_FILTERED: return 2;
+    default: break;
+  }
+  if ((long long)sizeof(long long) * g->V > g->l2_bytes / 2) return 0;
+  return g->E >= 8LL * g->V ? 2 : 1;
+}
+
 static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
                           int32_t* pred) {
   SsspArgs a{};
@@ -372,10 +388,7 @@ static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* ho
   a.phantom = g->tune.test_phantom_items;
   a.mark_neg_inf = g->tune.neg_cycle_mode == BFQ_NEG_CYCLE_MARK ? 1 : 0;
   a.cyc_walk0 = (unsigned)g->tune.cycle_walk_hops;
-  // one atomicMin per relaxation while the label array fits in half of L2
-  a.relax_min = g->tune.relax_atomic == BFQ_RELAX_MIN ? 1
-                : g->tune.relax_atomic == BFQ_RELAX_CAS ? 0
-                : (long long)sizeof(long long) * g->V <= g->l2_bytes / 2 ? 1 : 0;
+  a.relax_min = relax_form(g, g->tune.relax_atomic);
   a.wide = wide_form(g, g->tune);
   a.q_alloc = g->qs.Q;
   a.cq_alloc = g->cq.Q;
@@ -618,33 +631,31 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
       try_one(c);
     }
     {
-      // the other relaxation form (atomicMin pays while the labels stay in
-      // L2; near the half-of-L2 rule either may win)
-      bfq_tune c = best_t;
-      const bool min_now =
-          best_t.relax_atomic == BFQ_RELAX_MIN ||
-          (best_t.relax_atomic == BFQ_RELAX_AUTO &&
-           (long long)sizeof(long long) * g->V <= g->l2_bytes / 2);
-      c.relax_atomic = min_now ? BFQ_RELAX_CAS : BFQ_RELAX_MIN;
-      try_one(c);
+      // the other relaxation forms (atomicMin pays while the labels stay in
+      // L2, the filtered form where most relaxations fail; near the rules'
+      // edges any may win)
+      const bfq_tune base = best_t;
+      const int now = relax_form(g, base.relax_atomic);
+      for (int f = 0; f < 3; ++f)
+        if (f != now) {
+          bfq_tune c = base;
+          c.relax_atomic = kRelaxTuneOf[f];
+          try_one(c);
+        }
     }
     int max_persist = 0;
     cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device);
     cudaGetLastError();
     if (max_persist > 0) {
-      // with either relaxation form: a set-aside that keeps the labels from
+      // with every relaxation form: a set-aside that keeps the labels from
       // being evicted by the adjacency stream can make atomicMin pay where
       // it lost without one (labels near half of L2)
       const bfq_tune base = best_t;
-      const bool base_min =
-          base.relax_atomic == BFQ_RELAX_MIN ||
-          (base.relax_atomic == BFQ_RELAX_AUTO &&
-           (long long)sizeof(long long) * g->V <= g->l2_bytes / 2);
       for (int pct : {50, 75})
-        for (int other = 0; other < 2; ++other) {
+        for (int f = 0; f < 3; ++f) {
           bfq_tune c = base;
           c.l2_persist_pct = pct;
-          if (other) c.relax_atomic = base_min ? BFQ_RELAX_CAS : BFQ_RELAX_MIN;
+          c.relax_atomic = kRelaxTuneOf[f];
           try_one(c);
         }
     }

@@ -288,6 +288,9 @@ __global__ void relax_bench_fill_kernel(int2* edges, long long n_edges, int n_la
   for (long long v = tid; v < n_labels; v += nth) label[v] = kInfLabel;
 }
 
+// FILTER: load the label first and issue the atomicMin only when the key is
+// below it (the load-filtered relaxation form).
+template <bool FILTER>
 __global__ void relax_bench_kernel(const int2* __restrict__ edges, long long n_edges,
                                    long long* label, unsigned long long* lowered) {
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -300,8 +303,16 @@ __global__ void relax_bench_kernel(const int2* __restrict__ edges, long long n_e
     const int2 e1 = two ? __ldg(&edges[i + nth]) : make_int2(0, 0);
     const long long k0 = base_key + (long long)((unsigned long long)(long long)e0.y << 32);
     const long long k1 = base_key + (long long)((unsigned long long)(long long)e1.y << 32);
-    const long long o0 = atomicMin(&label[e0.x], k0 | kQueuedBit);
-    const long long o1 = two ? atomicMin(&label[e1.x], k1 | kQueuedBit) : k1;
+    long long o0, o1;
+    if (FILTER) {
+      o0 = ld_relaxed_s64(&label[e0.x]);
+      o1 = two ? ld_relaxed_s64(&label[e1.x]) : k1;
+      if (k0 < label_key(o0)) o0 = atomicMin(&label[e0.x], k0 | kQueuedBit);
+      if (two && k1 < label_key(o1)) o1 = atomicMin(&label[e1.x], k1 | kQueuedBit);
+    } else {
+      o0 = atomicMin(&label[e0.x], k0 | kQueuedBit);
+      o1 = two ? atomicMin(&label[e1.x], k1 | kQueuedBit) : k1;
+    }
     low += (k0 < label_key(o0)) + (two && k1 < label_key(o1));
   }
   low = __reduce_add_sync(kFullMask, (unsigned)low);
@@ -312,8 +323,9 @@ extern "C" {
 
 static int check_launch(int32_t grid, int32_t block, int64_t n);
 
-int bfq_relax_bench(int64_t n_edges, int32_t n_labels, int32_t grid, int32_t block,
-                    double* ms_out, int64_t* lowered_out, void* stream) {
+int bfq_relax_bench(int32_t mode, int64_t n_edges, int32_t n_labels, int32_t grid,
+                    int32_t block, double* ms_out, int64_t* lowered_out, void* stream) {
+  if (mode < 0 || mode > 1) return q_invalid("bfq_relax_bench: mode must be 0 or 1");
   if (n_edges < 1 || n_labels < 1) return q_invalid("bfq_relax_bench: n_edges and n_labels must be >= 1");
   int rc = check_launch(grid, block, n_edges);
   if (rc) return rc;
@@ -334,7 +346,10 @@ int bfq_relax_bench(int64_t n_edges, int32_t n_labels, int32_t grid, int32_t blo
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
   if (e == cudaSuccess) {
-    relax_bench_kernel<<<grid, block, 0, s>>>(edges, n_edges, label, low);
+    if (mode)
+      relax_bench_kernel<true><<<grid, block, 0, s>>>(edges, n_edges, label, low);
+    else
+      relax_bench_kernel<false><<<grid, block, 0, s>>>(edges, n_edges, label, low);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);

@@ -56,7 +56,12 @@ __device__ __forceinline__ bool flush_children(const SsspArgs& a, int home, unsi
 // label atomics, so the two round trips overlap.  Returns false on a timeout.
 // Claimed children are appended to the warp's buffer `buf` (nbuf items,
 // capacity kChildBuf) and published in bulk by flush_children.
-template <int U, bool MIN>
+// Relaxation forms of the single-query kernel (SsspArgs::relax_min).
+constexpr int kRelaxCas = 0;      // load, then compare-and-swap when lower
+constexpr int kRelaxMin = 1;      // one atomicMin per edge
+constexpr int kRelaxFilter = 2;   // load, then atomicMin only when lower
+
+template <int U, int RX>
 __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, int deg,
                                              long long lab, int tail, int lane, int home,
                                              WarpCounters& wc, unsigned* buf, int& nbuf,
@@ -120,11 +125,11 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
         const int c = edge_candidate(st->key0[own[g]], cw[g].y, &key[g]);
         if (c < 0) raise_status(a.ctl, kStRange);
         act[g] = c > 0;
-        if (act[g] && !MIN) cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
+        if (act[g] && RX != kRelaxMin) cur[g] = ld_relaxed_s64(&a.label[cw[g].x]);
       }
     }
     long long prev[U];
-    if (MIN) {
+    if (RX == kRelaxMin) {
       // One atomicMin per edge lowers the label and claims the in-queue flag
       // at once: keys are even (bit 0 is the flag), so key | 1 is below a
       // label exactly when key is below the label's key part, and the
@@ -134,6 +139,18 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       for (int g = 0; g < U; ++g) {
         prev[g] = 0;
         if (act[g]) cur[g] = atomicMin(&a.label[cw[g].x], key[g] | kQueuedBit);
+      }
+    } else if (RX == kRelaxFilter) {
+      // The same atomicMin, issued only where the label just loaded is
+      // above the key (labels only fall, so a stale load can only let an
+      // atomic through, never hold back a lowering one): where most
+      // relaxations fail, as on power-law graphs, loads take the place of
+      // atomics at L2; each lowering relaxation costs one round trip more.
+#pragma unroll
+      for (int g = 0; g < U; ++g) {
+        prev[g] = 0;
+        if (act[g] && key[g] < label_key(cur[g]))
+          cur[g] = atomicMin(&a.label[cw[g].x], key[g] | kQueuedBit);
       }
     } else {
       // Load, then the first compare-and-swap of every group back to back
@@ -156,7 +173,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
       enq[g] = false;
       if (act[g]) {
         const int r =
-            MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
+            RX != kRelaxCas ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
                         : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
                                               : lower_label(&a.label[cw[g].x], key[g], prev[g]);
         if (r) {
@@ -206,7 +223,7 @@ __device__ __forceinline__ bool relax_merged(const SsspArgs& a, int n, int beg, 
 
 // Publish the hub chunks [c0_j, c0_j + nch_j) of the lanes with nch > 0 to
 // the chunk sub-queues.  Chunks that find no room are relaxed right here.
-template <bool MIN>
+template <int RX>
 __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, int lane,
                                             int home, int chome, WarpCounters& wc,
                                             unsigned* buf, int& nbuf, unsigned& walk_at,
@@ -242,7 +259,7 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
         tail = ct.x;
         lab = label_key(ld_relaxed_s64(&a.label[ct.x]));
       }
-      if (!relax_merged<kGroups, MIN>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+      if (!relax_merged<kGroups, RX>(a, 1, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
                                       walk_at, st) ||
           !flush_children(a, home, buf, nbuf, lane, wc))
         return false;
@@ -252,15 +269,15 @@ __device__ __forceinline__ bool push_chunks(const SsspArgs& a, int nch, int c0, 
   return true;
 }
 
-// MIN: lower labels with one atomicMin per edge (see relax_merged).  CTAS:
+// RX: the relaxation form (kRelax*, see relax_merged).  CTAS:
 // the CTAs per SM the register budget is sized for: kCtasNarrow (64
 // registers per thread, more warps in flight) or kCtasWide (80 registers,
 // fewer spills; faster on low-degree graphs, whose warps spend more of each
-// step in queue operations).  All four forms are compiled; the launcher
+// step in queue operations).  All six forms are compiled; the launcher
 // picks one per run.
 constexpr int kCtasNarrow = BFQ_MIN_CTAS_PER_SM;
 constexpr int kCtasWide = 3;
-template <bool MIN, int CTAS>
+template <int RX, int CTAS>
 __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs a) {
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
       }
     }
     if (__any_sync(kFullMask, nch > 0)) {
-      if (!push_chunks<MIN>(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at, st)) {
+      if (!push_chunks<RX>(a, nch, c0, lane, home, chome, wc, buf, nbuf, walk_at, st)) {
         timed_out = true;
         break;
       }
@@ -379,7 +396,7 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
     // of the in-flight count: its children are counted before any becomes
     // visible, and the batch is done with; the labels are read by the
     // epilogue kernel, after this kernel has ended.
-    if (!relax_merged<kGroups, MIN>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
+    if (!relax_merged<kGroups, RX>(a, got, beg, deg, lab, tail, lane, home, wc, buf, nbuf,
                                     walk_at, st) ||
         !flush_children(a, home, buf, nbuf, lane, wc, got)) {
       timed_out = true;
@@ -559,11 +576,11 @@ __global__ void queue_reset_kernel(QueueSet qs) {
 
 // The persistent kernel in the form a.relax_min / a.wide name, with the L2
 // access-policy window as a launch attribute when one is given.
-template <bool MIN, int CTAS>
+template <int RX, int CTAS>
 cudaError_t launch_persistent_as(const SsspArgs& a, LaunchShape sh, cudaStream_t s,
                                  const cudaAccessPolicyWindow* l2win) {
   if (!l2win) {
-    sssp_persistent_kernel<MIN, CTAS><<<sh.grid, sh.block, 0, s>>>(a);
+    sssp_persistent_kernel<RX, CTAS><<<sh.grid, sh.block, 0, s>>>(a);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg{};
@@ -575,16 +592,20 @@ cudaError_t launch_persistent_as(const SsspArgs& a, LaunchShape sh, cudaStream_t
   attr[0].val.accessPolicyWindow = *l2win;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<MIN, CTAS>, a);
+  return cudaLaunchKernelEx(&cfg, sssp_persistent_kernel<RX, CTAS>, a);
 }
 
 cudaError_t launch_persistent(const SsspArgs& a, LaunchShape sh, cudaStream_t s,
                               const cudaAccessPolicyWindow* l2win) {
-  if (a.wide)
-    return a.relax_min ? launch_persistent_as<true, kCtasWide>(a, sh, s, l2win)
-                       : launch_persistent_as<false, kCtasWide>(a, sh, s, l2win);
-  return a.relax_min ? launch_persistent_as<true, kCtasNarrow>(a, sh, s, l2win)
-                     : launch_persistent_as<false, kCtasNarrow>(a, sh, s, l2win);
+  switch (a.relax_min * 2 + (a.wide ? 1 : 0)) {
+    case 0: return launch_persistent_as<kRelaxCas, kCtasNarrow>(a, sh, s, l2win);
+    case 1: return launch_persistent_as<kRelaxCas, kCtasWide>(a, sh, s, l2win);
+    case 2: return launch_persistent_as<kRelaxMin, kCtasNarrow>(a, sh, s, l2win);
+    case 3: return launch_persistent_as<kRelaxMin, kCtasWide>(a, sh, s, l2win);
+    case 4: return launch_persistent_as<kRelaxFilter, kCtasNarrow>(a, sh, s, l2win);
+    case 5: return launch_persistent_as<kRelaxFilter, kCtasWide>(a, sh, s, l2win);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -593,9 +614,9 @@ int sssp_max_ctas_per_sm(int block, int wide) {
   int n = 0;
   const cudaError_t e =
       wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                 &n, sssp_persistent_kernel<true, kCtasWide>, block, 0)
+                 &n, sssp_persistent_kernel<kRelaxMin, kCtasWide>, block, 0)
            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                 &n, sssp_persistent_kernel<true, kCtasNarrow>, block, 0);
+                 &n, sssp_persistent_kernel<kRelaxMin, kCtasNarrow>, block, 0);
   if (e != cudaSuccess) return 1;
   return n < 1 ? 1 : n;
 }

@@ -90,6 +90,15 @@ def test_random_with_cycles_cas_relaxation(seed):
 
 
 @pytest.mark.parametrize("seed", range(6))
+def test_random_with_cycles_filtered_relaxation(seed):
+    rng = np.random.default_rng(60 + seed)
+    V = int(rng.integers(100, 3000))
+    g = synth.random_graph(V, 9 * V, seed=920 + seed, wlo=-3, whi=40)
+    t = bfq.make_tune(neg_cycle_mode=bfq.NEG_CYCLE_MARK, relax_atomic=bfq.RELAX_FILTERED)
+    _compare(g, 0, gpu_util.sssp(g, 0, tune=t, want_pred=True), check_pred=True)
+
+
+@pytest.mark.parametrize("seed", range(6))
 def test_random_with_cycles_single_shot_queues(seed):
     """Minus-infinity marking with single-shot sub-queues (children published
     in the same round trips as the next dequeue)."""

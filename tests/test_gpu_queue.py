@@ -137,12 +137,14 @@ def test_atomic_bench_rejects_bad_arguments():
             bfq.bfq_atomic_bench(*args)
 
 
-def test_relax_bench_runs_and_counts():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_relax_bench_runs_and_counts(mode):
     """The relaxation-pattern microbenchmark touches every edge once: with
-    labels starting at infinity, at least one atomic per distinct label
-    lowers it, and no more atomics than edges do."""
+    labels starting at infinity, at least one edge per distinct label
+    lowers it, and no more edges than there are do."""
     n, L = 1 << 20, 1 << 16
-    ms, low = bfq.bfq_relax_bench(n, L, 152 * 4, 256)
+    ms, low = bfq.bfq_relax_bench(mode, n, L, 152 * 4, 256)
     assert ms > 0 and L // 2 <= low <= n
-    with pytest.raises(bfq.BfqError):
-        bfq.bfq_relax_bench(0, L, 8, 64)
+    for bad in ((mode, 0, L, 8, 64), (2, n, L, 8, 64), (-1, n, L, 8, 64)):
+        with pytest.raises(bfq.BfqError):
+            bfq.bfq_relax_bench(*bad)

@@ -136,6 +136,9 @@ def test_rmat22_full_all_sources():
     dict(queue_form=2, kernel_ctas=3),
     dict(queue_form=2, hub_degree=32, chunk_edges=32, batch_items=4, queues_per_cta=4),
     dict(queue_form=2, relax_atomic=2, ctas_per_sm=1),
+    dict(relax_atomic=3),
+    dict(relax_atomic=3, kernel_ctas=3, hub_degree=32, chunk_edges=32, batch_items=4),
+    dict(relax_atomic=3, queue_form=2, queues_per_cta=4),
 ], ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
 def test_tunes(tune):
     g = synth.workload_rmat(14)
@@ -355,7 +358,7 @@ def test_planted_cycle_detected_fast_on_large_graph():
         bfq.bfq_graph_destroy(h)
 
 
-@pytest.mark.parametrize("relax", [1, 2])
+@pytest.mark.parametrize("relax", [1, 2, 3])
 @pytest.mark.parametrize("walk", [2, 8, 64, 1 << 30])
 def test_cycle_walk_threshold_changes_speed_only(walk, relax):
     """Every first-walk threshold gives the same answers: exact labels on a
@@ -391,6 +394,30 @@ def test_queue_forms_full_size_and_cycles(form):
                 _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
             t = bfq.bfq_graph_get_tune(h)
             t.queue_form = 3 - form
+            bfq.bfq_graph_set_tune(h, t)
+            _compare(g, int(srcs[0]), gpu_util.run(h, g.V, int(srcs[0])))
+        finally:
+            bfq.bfq_graph_destroy(h)
+
+
+@pytest.mark.parametrize("form", [bfq.RELAX_MIN, bfq.RELAX_CAS, bfq.RELAX_FILTERED])
+def test_relax_forms_full_size_and_cycles(form):
+    """Each relaxation form (atomicMin, compare-and-swap, load-filtered
+    atomicMin) gives the oracle's results on R-MAT 22, the road-like grid
+    and a planted cycle, and a switch to the next form on one handle meets
+    no stale state."""
+    rm = synth.workload_rmat(22)
+    road = synth.workload_road1m()
+    cyc = synth.plant_negative_cycle(synth.grid_graph(50, 50, seed=3), 5, seed=2)
+    nxt = {bfq.RELAX_MIN: bfq.RELAX_CAS, bfq.RELAX_CAS: bfq.RELAX_FILTERED,
+           bfq.RELAX_FILTERED: bfq.RELAX_MIN}[form]
+    for g, srcs in ((rm, rm.sources[:1]), (road, road.sources[:2]), (cyc, [0])):
+        h = gpu_util.create(g, bfq.make_tune(relax_atomic=form))
+        try:
+            for s in srcs:
+                _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
+            t = bfq.bfq_graph_get_tune(h)
+            t.relax_atomic = nxt
             bfq.bfq_graph_set_tune(h, t)
             _compare(g, int(srcs[0]), gpu_util.run(h, g.V, int(srcs[0])))
         finally:
