@@ -346,8 +346,12 @@ static int wide_form(bfq_graph_t g, const bfq_tune& t) {
 
 // Relaxation form of the persistent kernel (SsspArgs::relax_min: 0 CAS,
 // 1 atomicMin, 2 filtered atomicMin).  AUTO: atomicMin while the label array
-// fits in half of L2, filtered from an average out-degree of 8, where most
-// relaxations fail; compare-and-swap once the labels outgrow L2.
+// fits in half of L2; filtered instead on large graphs (2^21 vertices or
+// more) of average out-degree 8 or more, where most relaxations fail and L2
+// atomic throughput, not the extra round trip of a lowering relaxation,
+// sets the pace (measured on R-MAT: atomicMin 20% faster at 2^18 vertices,
+// even at 2^20, filtered 7% faster at 2^21 and 2^22); compare-and-swap once
+// the labels outgrow L2.
 static const int32_t kRelaxTuneOf[3] = {BFQ_RELAX_CAS, BFQ_RELAX_MIN, BFQ_RELAX_FILTERED};
 static int relax_form(bfq_graph_t g, int32_t relax_atomic) {
   switch (relax_atomic) {
@@ -357,7 +361,7 @@ static int relax_form(bfq_graph_t g, int32_t relax_atomic) {
     default: break;
   }
   if ((long long)sizeof(long long) * g->V > g->l2_bytes / 2) return 0;
-  return g->E >= 8LL * g->V ? 2 : 1;
+  return (g->V >= (1 << 21) && g->E >= 8LL * g->V) ? 2 : 1;
 }
 
 static SsspArgs make_args(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops,
