@@ -122,10 +122,10 @@ typedef struct bfq_tune {
                                (load, then atomicMin only when lower: fewer
                                atomics where most relaxations fail) or
                                BFQ_RELAX_CAS (load, then compare-and-swap
-                               only when lower).  AUTO takes FILTERED when
-                               8 V <= half of L2, V >= 2^21 and E >= 8 V,
-                               MIN when 8 V <= half of L2 otherwise, else
-                               CAS.
+                               only when lower).  AUTO takes MIN when 8 V <=
+                               half of L2, except FILTERED there for V >=
+                               2^21 and E >= 8 V, and FILTERED when 8 V is
+                               above half of L2.
                                Results are the same in every form.           */
   int32_t batch_budget_klabels; /* batched queries: labels (in units of 1024)
                                of the queries running at once.  Queries start

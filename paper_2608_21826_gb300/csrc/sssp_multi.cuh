@@ -82,7 +82,8 @@ struct MultiStage {
 // label atomics.  MIN: one atomicMin per edge lowers the label and claims the
 // in-queue flag (keys are even, so key | 1 is below a label exactly when key
 // is below its key part); for labels that stay in L2, since every atomic
-// dirties its line.  Otherwise load, then compare-and-swap when lower.
+// dirties its line.  Otherwise load, then the same atomicMin only when the
+// key is below the loaded label (a stale load is only ever too high).
 template <int U, bool MIN>
 __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2* eptr, int deg,
                                             long long lab, long long* lbase, int Vq, int q,
@@ -155,23 +156,15 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
         if (act[g] && !MIN) cur[g] = ld_relaxed_s64(st->lbase[own[g]] + cw[g].x);
       }
     }
-    long long prev[U];
     if (MIN) {
 #pragma unroll
-      for (int g = 0; g < U; ++g) {
-        prev[g] = 0;
+      for (int g = 0; g < U; ++g)
         if (act[g]) cur[g] = atomicMin(st->lbase[own[g]] + cw[g].x, key[g] | kQueuedBit);
-      }
     } else {
-      // first compare-and-swap of every group back to back (they overlap);
-      // a failed one retries through lower_label
 #pragma unroll
       for (int g = 0; g < U; ++g) {
-        prev[g] = cur[g];
         if (act[g] && key[g] < label_key(cur[g]))
-          prev[g] = (long long)atomicCAS((unsigned long long*)(st->lbase[own[g]] + cw[g].x),
-                                         (unsigned long long)cur[g],
-                                         (unsigned long long)(key[g] | kQueuedBit));
+          cur[g] = atomicMin(st->lbase[own[g]] + cw[g].x, key[g] | kQueuedBit);
         else
           act[g] = false;
       }
@@ -182,10 +175,7 @@ __device__ __forceinline__ bool relax_multi(const MultiEnv& e, int n, const int2
       enq[g] = false;
       if (act[g]) {
         long long* lb = st->lbase[own[g]];
-        const int r =
-            MIN ? (key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0)
-                : (prev[g] == cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2)
-                                      : lower_label(lb + cw[g].x, key[g], prev[g]);
+        const int r = key[g] < label_key(cur[g]) ? ((cur[g] & kQueuedBit) ? 1 : 2) : 0;
         if (r) {
           ++wc.upd;
           const unsigned nh = label_hops(key[g]);
