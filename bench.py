@@ -883,21 +883,42 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        host_dist = torch.empty(V, dtype=torch.int32, pin_memory=True)
+        # through the public C ABI with results read back to pinned host
+        # memory: each step's queries are enqueued back to back with
+        # bfq_sssp_async (the status codes and every query's dist copied to
+        # the host on the same stream) and the step ends with one
+        # synchronisation; the host-synchronous bfq_sssp per query, with its
+        # copy, is reported beside it
+        stream = torch.cuda.current_stream(dev)
+        host_dist = [torch.empty(V, dtype=torch.int32, pin_memory=True) for _ in srcs]
+        status_dev = torch.zeros(len(srcs), dtype=torch.int32, device=dev)
+        status_host = torch.empty(len(srcs), dtype=torch.int32, pin_memory=True)
         t0 = time.perf_counter()
-        m_e2e = 0
         for _ in range(args.steps):
-            for s in srcs:
+            for i, s in enumerate(srcs):
+                bfq.bfq_sssp_async(h, s, dist_t, None, None, status_dev[i:i + 1], stream)
+                host_dist[i].copy_(dist_t, non_blocking=True)    # result to pinned host
+            status_host.copy_(status_dev, non_blocking=True)
+            stream.synchronize()
+            if bool((status_host != bfq.OK).any()):
+                raise SystemExit(f"bench e2e: status {status_host.tolist()}")
+        t_e2e = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for i, s in enumerate(srcs):
                 st = bfq.bfq_sssp(h, s, dist_t)                # host-synchronous C-ABI call
-                host_dist.copy_(dist_t, non_blocking=False)      # result to pinned host
+                host_dist[i].copy_(dist_t, non_blocking=False)
                 if st != bfq.OK:
                     raise SystemExit(f"bench e2e: status {st}")
-        t_e2e = time.perf_counter() - t0
+        t_sync = time.perf_counter() - t0
         m_e2e = m_reached                                        # same queries, same graph
         e2e = {"value": m_e2e / t_e2e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * len(srcs), "d2h_bytes_per_step": (4 * V + 4) * len(srcs),
-               "note": "bfq_sssp (host-synchronous) per source + copy of dist to pinned host; "
-                       "sources pass by value, the graph is resident"}
+               "sync_value": m_e2e / t_sync / 1e9,
+               "note": "per step: bfq_sssp_async per source, each query's dist and status copied "
+                       "to pinned host on the same stream, one synchronisation; sync_value: "
+                       "bfq_sssp (host-synchronous) per source + its copy; sources pass by "
+                       "value, the graph is resident"}
     # clocks seen over both timed regions (device-timed and end to end)
     clk = clocks.stop()
 
