@@ -148,6 +148,18 @@ typedef struct bfq_tune {
                                (the Broker Work Distributor's ensure-once: one
                                fetch-add on one of two counters, no retry).
                                Results are the same either way.             */
+  int32_t small_path;       /* BFQ_SMALL_PATH_AUTO, _ON or _OFF: run bfq_sssp /
+                               bfq_sssp_async on one CTA whose shared memory
+                               holds the labels, the recorded relaxation
+                               edges and the vertex queue (the same queue-
+                               driven algorithm at CTA scope; the CSR is read
+                               from global memory).  Only when they fit
+                               (16 B per vertex plus the queue ring: about
+                               8,000 vertices on GB300) and neg_cycle_mode is
+                               STOP; otherwise the persistent kernel runs.
+                               AUTO takes it for graphs of at most 32,768
+                               edges (that fit).
+                               Results are the same either way.             */
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a
@@ -169,6 +181,11 @@ typedef struct bfq_tune {
 #define BFQ_QUEUE_FORM_AUTO 0
 #define BFQ_QUEUE_FORM_EXACT 1
 #define BFQ_QUEUE_FORM_SINGLE_SHOT 2
+
+/* bfq_tune.small_path */
+#define BFQ_SMALL_PATH_AUTO 0
+#define BFQ_SMALL_PATH_ON 1
+#define BFQ_SMALL_PATH_OFF 2
 
 /* bfq_tune.relax_atomic */
 #define BFQ_RELAX_AUTO 0
@@ -318,15 +335,17 @@ int bfq_graph_set_tune(bfq_graph_t g, const bfq_tune* t);
 
 
 /* Pick the run-time parameters (share_div, chunk_batch, batch_items, then
- * kernel_ctas, queue_form, relax_atomic and l2_persist_pct) that make the
- * queries from srcs[0..n) (host array) fastest on g, keep them on the handle
- * and copy them to *out (nullable).  Times a fixed grid of candidates in the
- * handle's register form over one pass of the sources each, the best four
- * again over four passes, then, one at a time at the best so far, the other
- * register form, the other queue form, the other relaxation form, and an L2
- * set-aside of 50 and 75 percent for the labels with either relaxation form
- * (CUDA events, each pass after an untimed one); allocates one int32[V]
- * scratch array for the duration.  Synchronises `stream`. */
+ * kernel_ctas, queue_form, relax_atomic, l2_persist_pct and small_path) that
+ * make the queries from srcs[0..n) (host array) fastest on g, keep them on
+ * the handle and copy them to *out (nullable).  Times a fixed grid of
+ * candidates in the handle's register form over one pass of the sources
+ * each, the best four again over four passes, then, one at a time at the
+ * best so far, the other register form, the other queue form, the other
+ * relaxation forms, an L2 set-aside of 50 and 75 percent for the labels with
+ * each relaxation form, and, where the graph fits, the other of the
+ * single-CTA and persistent paths (CUDA events, each pass after an untimed
+ * one); allocates one int32[V] scratch array for the duration.
+ * Synchronises `stream`. */
 int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, void* stream);
 
 /* ---- batched queries: many sources over many resident graphs in one

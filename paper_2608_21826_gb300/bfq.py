@@ -38,7 +38,8 @@ class Tune(ctypes.Structure):
                 ("share_div", ctypes.c_int32), ("chunk_batch", ctypes.c_int32),
                 ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
                 ("relax_atomic", ctypes.c_int32), ("batch_budget_klabels", ctypes.c_int32),
-                ("kernel_ctas", ctypes.c_int32), ("queue_form", ctypes.c_int32)]
+                ("kernel_ctas", ctypes.c_int32), ("queue_form", ctypes.c_int32),
+                ("small_path", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -62,6 +63,7 @@ class RoundsStats(ctypes.Structure):
 ROUNDS_ALL_EDGES = 1
 NEG_CYCLE_STOP, NEG_CYCLE_MARK = 0, 1
 RELAX_AUTO, RELAX_MIN, RELAX_CAS, RELAX_FILTERED = 0, 1, 2, 3
+SMALL_PATH_AUTO, SMALL_PATH_ON, SMALL_PATH_OFF = 0, 1, 2
 NEG_INF = -2147483648          # dist of a vertex reachable from a negative cycle (MARK)
 
 _VP = ctypes.c_void_p

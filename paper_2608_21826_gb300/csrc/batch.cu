@@ -214,17 +214,23 @@ __global__ void __launch_bounds__(kBlock, BFQ_MULTI_CTAS_PER_SM) batch_persisten
     }
     if (got < 0) { timed_out = true; break; }
     if (got == 0) {
+      // lane 0 decides whether the warp leaves (done, or out of time) and
+      // the warp follows as one: lanes may run apart after a sleep
       int done = 0;
-      if (lane == 0)
+      if (lane == 0) {
         done = (ld_relaxed_s32(&a.ctl->remaining) <= 0) || ld_relaxed_s32(&a.ctl->stop);
-      if (__shfl_sync(kFullMask, done, 0)) break;
+        if (!done && ((idle + 1) & 31) == 0 &&
+            (long long)(globaltimer_ns() - t_start) > hdr.time_limit_ns)
+          done = 2;
+      }
+      done = __shfl_sync(kFullMask, done, 0);
+      if (done) {
+        timed_out = done == 2;
+        break;
+      }
       ++wc.idle;
       __nanosleep(min(32u << min(idle, 6), 2048u));
       ++idle;
-      if ((idle & 31) == 0 && (long long)(globaltimer_ns() - t_start) > hdr.time_limit_ns) {
-        timed_out = true;
-        break;
-      }
       continue;
     }
     idle = 0;

@@ -95,6 +95,19 @@ cudaError_t launch_sssp_persistent_only(const SsspArgs& a, LaunchShape run_shape
 cudaError_t launch_sssp_epilogue(const SsspArgs& a, LaunchShape shape, int32_t* status_dev,
                                  const int* bad, cudaStream_t s);
 
+// Single-CTA query for small graphs (sssp_small.cu): dynamic shared memory
+// of a run over V vertices with a ring of 2^cap_log2 slots, the most the
+// device allows (sets the kernel attribute; 0 if unavailable), and the run
+// (kernel bracketed by ev0/ev1 when given, then the epilogue).
+size_t sssp_small_smem(int V, int cap_log2);
+size_t sssp_small_smem_limit();
+cudaError_t launch_sssp_small(const SsspArgs& a, int cap_log2, int32_t* status_dev,
+                              cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s);
+
+// The run's predecessor pass (a.pred), after its epilogue: skipped, leaving
+// -1, when the run did not end clean.
+cudaError_t launch_sssp_pred(const SsspArgs& a, cudaStream_t s);
+
 // Predecessor pass alone over final labels (pred must hold -1 beforehand).
 cudaError_t launch_pred_pass(const int* row_ptr, const int2* adj, const long long* label, int V,
                              int* pred, cudaStream_t s);

@@ -61,6 +61,7 @@ struct bfq_graph {
   LaunchShape run_shape{};                     // the workspace's shape (narrow form)
   int sms = 0;
   int per_sm_wide = 0;                         // CTAs per SM of the wide form
+  size_t small_smem_limit = 0;                 // dynamic shared memory of the small path
   LaunchShape last_shape{};                    // the last run's shape and
   int last_queues = 0;                         //   vertex sub-queues (stats)
   long long bytes = 0;
@@ -164,6 +165,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   out->relax_atomic = in->relax_atomic;
   out->kernel_ctas = in->kernel_ctas;
   out->queue_form = in->queue_form;
+  out->small_path = in->small_path;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 (the shared-memory layout of the kernels)");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -181,7 +183,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       out->cycle_walk_hops < 2 || out->cycle_walk_hops > (1 << 30) ||
       out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_FILTERED ||
       (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4) ||
-      out->queue_form < BFQ_QUEUE_FORM_AUTO || out->queue_form > BFQ_QUEUE_FORM_SINGLE_SHOT)
+      out->queue_form < BFQ_QUEUE_FORM_AUTO || out->queue_form > BFQ_QUEUE_FORM_SINGLE_SHOT ||
+      out->small_path < BFQ_SMALL_PATH_AUTO || out->small_path > BFQ_SMALL_PATH_OFF)
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -290,6 +293,7 @@ int bfq_graph_create(bfq_graph_t* out, int32_t V, int64_t E, const int32_t* row_
   // the wide form fits fewer CTAs: it runs on a prefix of the sub-queues
   g->per_sm_wide = std::min(per_sm, sssp_max_ctas_per_sm(block, 1));
   g->init_shape = {sms * 4, 256};
+  g->small_smem_limit = sssp_small_smem_limit();
 
   // workspace: labels (with in-queue flags), vertex and chunk sub-queues
   const int Q = g->run_shape.grid * g->tune.queues_per_cta;
@@ -442,6 +446,28 @@ static int apply_l2_window(bfq_graph_t g) {
   return BFQ_OK;
 }
 
+// Ring of the small path: a power of two >= V (at most V vertices are queued
+// at once), at least one warp's worth.
+static int small_cap_log2(int V) { return std::max(5, ceil_log2(V)); }
+
+// Whether a query runs on the single-CTA path: asked for or AUTO, it fits
+// in shared memory, and cycles stop the run.  AUTO: up to 32K edges, where
+// one SM keeps up with the work and the search's depth, not its width, sets
+// the time (measured against the persistent kernel: the 64x64 grid 0.46
+// against 0.82 ms, a 64x64 road-like grid 0.15 against 0.22 ms, and 9 of
+// the batched mix's 10 graphs up to 32K edges 30-50% faster, the tenth 7%
+// slower; above that the single SM falls behind, e.g. 8K vertices and
+// 40K-80K edges 15-50% slower).
+static bool small_path_fits(bfq_graph_t g, const bfq_tune& t) {
+  return t.neg_cycle_mode != BFQ_NEG_CYCLE_MARK &&
+         sssp_small_smem(g->V, small_cap_log2(g->V)) <= g->small_smem_limit;
+}
+static bool use_small_path(bfq_graph_t g, const bfq_tune& t) {
+  if (t.small_path == BFQ_SMALL_PATH_OFF || !small_path_fits(g, t)) return false;
+  if (t.small_path == BFQ_SMALL_PATH_ON) return true;
+  return g->E <= 32768;
+}
+
 int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int32_t* pred,
                    int32_t* status_dev, void* stream) {
   if (!g) return invalid("bfq_sssp: null graph handle");
@@ -449,6 +475,14 @@ int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int
   if (!dist) return invalid("bfq_sssp: dist is null");
   cudaStream_t s = (cudaStream_t)stream;
   g->last_stream = s;
+  if (use_small_path(g, g->tune)) {
+    SsspArgs a = make_args(g, src, dist, hops, pred);
+    g->last_shape = LaunchShape{1, 1024};
+    g->last_queues = 1;
+    BFQ_CUDA_TRY(launch_sssp_small(a, small_cap_log2(g->V), status_dev, g->ev0, g->ev1, s));
+    if (pred) BFQ_CUDA_TRY(launch_sssp_pred(a, s));
+    return BFQ_OK;
+  }
   const cudaAccessPolicyWindow* win = nullptr;
   if (g->tune.l2_persist_pct > 0) {
     const int rc = apply_l2_window(g);
@@ -664,6 +698,13 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
           c.relax_atomic = kRelaxTuneOf[f];
           try_one(c);
         }
+    }
+    if (small_path_fits(g, best_t)) {
+      // the other path: one CTA with the search state in shared memory, or
+      // the persistent kernel
+      bfq_tune c = best_t;
+      c.small_path = use_small_path(g, best_t) ? BFQ_SMALL_PATH_OFF : BFQ_SMALL_PATH_ON;
+      try_one(c);
     }
   }
   cudaStreamSynchronize(s);

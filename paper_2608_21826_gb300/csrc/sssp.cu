@@ -343,18 +343,23 @@ __global__ void __launch_bounds__(kBlock, CTAS) sssp_persistent_kernel(SsspArgs 
     }
     if (got < 0) { timed_out = true; break; }
     if (got == 0) {
+      // lane 0 decides whether the warp leaves (done, or out of time) and
+      // the warp follows as one: lanes may run apart after a sleep
       int done = 0;
-      if (lane == 0)
+      if (lane == 0) {
         done = (ld_relaxed_s32(&a.ctl->inflight) == 0) || ld_relaxed_s32(&a.ctl->stop);
-      if (__shfl_sync(kFullMask, done, 0)) break;
+        if (!done && ((idle + 1) & 31) == 0 &&
+            (long long)(globaltimer_ns() - t_start) > a.time_limit_ns)
+          done = 2;
+      }
+      done = __shfl_sync(kFullMask, done, 0);
+      if (done) {
+        timed_out = done == 2;
+        break;
+      }
       ++wc.idle;
       __nanosleep(min(32u << min(idle, 6), 2048u));
       ++idle;
-      if ((idle & 31) == 0 &&
-          (long long)(globaltimer_ns() - t_start) > a.time_limit_ns) {
-        timed_out = true;
-        break;
-      }
       continue;
     }
     idle = 0;
@@ -639,6 +644,12 @@ cudaError_t launch_sssp(const SsspArgs& a, LaunchShape init_shape, LaunchShape r
 cudaError_t launch_pred_pass(const int* row_ptr, const int2* adj, const long long* label, int V,
                              int* pred, cudaStream_t s) {
   sssp_pred_kernel<<<1024, 256, 0, s>>>(row_ptr, adj, label, V, pred, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sssp_pred(const SsspArgs& a, cudaStream_t s) {
+  sssp_pred_kernel<<<1024, 256, 0, s>>>(a.row_ptr, a.adj, a.label, a.V, a.pred, a.ctl,
+                                        a.mark_neg_inf);
   return cudaGetLastError();
 }
 

@@ -24,23 +24,30 @@ def _compare(g, src, res, check_pred=False):
     return ost
 
 
+# the persistent kernel explicitly (small graphs run on the single-CTA path by
+# default, which tests/test_gpu_small.py covers)
+PERSISTENT = bfq.make_tune(small_path=bfq.SMALL_PATH_OFF)
+
+
+@pytest.mark.parametrize("tune", [None, PERSISTENT], ids=["auto", "persistent"])
 @pytest.mark.parametrize("path", helpers.golden_files(), ids=lambda p: p.split("/")[-1])
-def test_golden(path):
+def test_golden(path, tune):
     g, exp = helpers.load_golden(path)
-    st, d, h, p = gpu_util.sssp(g, 0, want_pred=True)
+    st, d, h, p = gpu_util.sssp(g, 0, tune=tune, want_pred=True)
     assert st == exp["status"]
     if "dist" in exp:
         assert d.tolist() == exp["dist"] and h.tolist() == exp["hops"]
         assert oracle.check_pred(g.row_ptr, g.col, g.w, 0, d, p)
 
 
+@pytest.mark.parametrize("tune", [None, PERSISTENT], ids=["auto", "persistent"])
 @pytest.mark.parametrize("seed", range(30))
-def test_random_with_cycles(seed):
+def test_random_with_cycles(seed, tune):
     rng = np.random.default_rng(seed)
     V = int(rng.integers(1, 3000))
     E = int(rng.integers(0, 6 * V + 1))
     g = synth.random_graph(V, E, seed=500 + seed, wlo=-3, whi=40)
-    _compare(g, 0, gpu_util.sssp(g, 0))
+    _compare(g, 0, gpu_util.sssp(g, 0, tune=tune))
 
 
 @pytest.mark.parametrize("seed", range(10))
@@ -169,15 +176,16 @@ def test_long_path():
     assert np.array_equal(d, np.r_[0, np.cumsum(w)]) and np.array_equal(h, np.arange(V))
 
 
-def test_single_vertex_and_no_edges():
+@pytest.mark.parametrize("tune", [None, PERSISTENT], ids=["auto", "persistent"])
+def test_single_vertex_and_no_edges(tune):
     g = synth.Graph("one", np.array([0, 0], np.int32), np.zeros(0, np.int32),
                     np.zeros(0, np.int32), np.array([0], np.int32))
-    st, d, h, p = gpu_util.sssp(g, 0, want_pred=True)
+    st, d, h, p = gpu_util.sssp(g, 0, tune=tune, want_pred=True)
     assert st == bfq.OK and d.tolist() == [0] and h.tolist() == [0] and p.tolist() == [-1]
     rp = np.zeros(1001, np.int32)
     g = synth.Graph("empty", rp, np.zeros(0, np.int32), np.zeros(0, np.int32),
                     np.array([0], np.int32))
-    st, d, h, _ = gpu_util.sssp(g, 500)
+    st, d, h, _ = gpu_util.sssp(g, 500, tune=tune)
     assert st == bfq.OK and d[500] == 0 and np.sum(d == INF) == 999
 
 
@@ -200,7 +208,7 @@ def test_cycle_then_clean_on_one_handle():
                       potential=np.r_[base.potential, base.potential])
     g = synth.plant_negative_cycle(two, 5, seed=3, reachable_from=[V])   # in copy 2
     assert np.all(g.cycle >= V)
-    h = gpu_util.create(g)
+    h = gpu_util.create(g, PERSISTENT)
     try:
         for src in (V, 0, V + 17, 5, 0):
             res = gpu_util.run(h, g.V, src)
@@ -228,7 +236,7 @@ def test_register_forms_switch_on_one_handle():
     form; the next run, in either form, must reset every sub-queue and be
     exact; the stats report the grid of the form that ran."""
     g, V = _two_copies_cycle_in_second()
-    h = gpu_util.create(g)
+    h = gpu_util.create(g, PERSISTENT)
     try:
         grids = {}
         seq = [(4, V), (3, 0), (3, V + 11), (4, 0), (4, 7), (3, V), (3, 5), (4, V + 3), (4, 9)]
@@ -329,13 +337,14 @@ def _path_into_cycle(n_path, cyc_w, seed=0):
     return synth.Graph("pathcycle", rp, col, np.array(ww, np.int32)[order], np.array([0], np.int32))
 
 
+@pytest.mark.parametrize("tune", [None, PERSISTENT], ids=["auto", "persistent"])
 @pytest.mark.parametrize("cyc_w", [-1, 0, 3])
-def test_cycle_accelerator_sound_and_fast(cyc_w):
+def test_cycle_accelerator_sound_and_fast(cyc_w, tune):
     """A deep path feeding a 5-cycle: the hop counts pass the walk threshold,
     so the recorded-edge walk runs; it must report only a negative cycle (the
     zero and positive ones are not), and quickly."""
     g = _path_into_cycle(3000, cyc_w)
-    h = gpu_util.create(g)
+    h = gpu_util.create(g, tune)
     try:
         res = gpu_util.run(h, g.V, 0)
         ost = _compare(g, 0, res)
@@ -364,7 +373,8 @@ def test_cycle_walk_threshold_changes_speed_only(walk, relax):
     """Every first-walk threshold gives the same answers: exact labels on a
     clean deep graph, BFQ_NEG_CYCLE with a planted cycle (at 2^30 only the
     hops >= V test is left)."""
-    t = bfq.make_tune(cycle_walk_hops=walk, relax_atomic=relax)
+    t = bfq.make_tune(cycle_walk_hops=walk, relax_atomic=relax,
+                      small_path=bfq.SMALL_PATH_OFF)
     clean = synth.road_graph(128, seed=3)
     _compare(clean, 0, gpu_util.sssp(clean, 0, tune=t))
     g = synth.plant_negative_cycle(synth.grid_graph(48, 48, seed=4), 5, seed=6)
@@ -388,7 +398,7 @@ def test_queue_forms_full_size_and_cycles(form):
     rm = synth.workload_rmat(16)
     cyc = synth.plant_negative_cycle(synth.grid_graph(50, 50, seed=3), 5, seed=2)
     for g, srcs in ((road, road.sources[:2]), (rm, rm.sources[:2]), (cyc, [0])):
-        h = gpu_util.create(g, bfq.make_tune(queue_form=form))
+        h = gpu_util.create(g, bfq.make_tune(queue_form=form, small_path=bfq.SMALL_PATH_OFF))
         try:
             for s in srcs:
                 _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
@@ -412,7 +422,7 @@ def test_relax_forms_full_size_and_cycles(form):
     nxt = {bfq.RELAX_MIN: bfq.RELAX_CAS, bfq.RELAX_CAS: bfq.RELAX_FILTERED,
            bfq.RELAX_FILTERED: bfq.RELAX_MIN}[form]
     for g, srcs in ((rm, rm.sources[:1]), (road, road.sources[:2]), (cyc, [0])):
-        h = gpu_util.create(g, bfq.make_tune(relax_atomic=form))
+        h = gpu_util.create(g, bfq.make_tune(relax_atomic=form, small_path=bfq.SMALL_PATH_OFF))
         try:
             for s in srcs:
                 _compare(g, int(s), gpu_util.run(h, g.V, int(s)))
@@ -430,7 +440,7 @@ def test_single_shot_random_and_edge_cases(seed):
     the same round trips as their next dequeue) on random graphs with and
     without cycles, a hub star, a long path and the golden fixtures."""
     rng = np.random.default_rng(300 + seed)
-    t = bfq.make_tune(queue_form=2)
+    t = bfq.make_tune(queue_form=2, small_path=bfq.SMALL_PATH_OFF)
     V = int(rng.integers(1, 4000))
     g = (synth.random_graph(V, int(rng.integers(0, 4 * V + 1)), seed=seed, wlo=-3, whi=40)
          if seed % 2 else synth.random_potential_graph(max(2, V), 5 * max(2, V), seed=seed))
