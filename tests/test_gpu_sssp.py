@@ -63,9 +63,10 @@ def test_tie_heavy():
     _compare(g, 0, gpu_util.sssp(g, 0, want_pred=True), check_pred=True)
 
 
-def test_grid4k_full():
+@pytest.mark.parametrize("tune", [None, PERSISTENT], ids=["auto", "persistent"])
+def test_grid4k_full(tune):
     g = synth.workload_grid4k()
-    h = gpu_util.create(g)
+    h = gpu_util.create(g, tune)
     try:
         res = gpu_util.run(h, g.V, 0, want_pred=True)
         _compare(g, 0, res, check_pred=True)
