@@ -72,6 +72,14 @@ def parse_args(argv=None):
     return p.parse_args(argv)
 
 
+def workload_label(args):
+    """The workload's name in the JSON line and the profile lookup: the R-MAT
+    workload is named by the scale it ran at."""
+    if args.workload == "rmat22" and args.rmat_scale != 22:
+        return f"rmat{args.rmat_scale}"
+    return args.workload
+
+
 def load_workload(name, rmat_scale=22):
     from paper_2608_21826_gb300 import synth
     if name == "rmat22":
@@ -784,7 +792,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "V": g.V, "E": g.E,
+        "config": {"workload": workload_label(args), "desc": desc, "V": g.V, "E": g.E,
                    "step": "one single-source query (sources rotate)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} single-source queries on 1 core of "
@@ -879,7 +887,7 @@ def run_ours(args):
     k_s = sum(k_ms) / 1e3
     achieved = b_eff / k_s / 1e9
     peak, peak_src = measured_peak_hbm()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(workload_label(args))
 
     e2e = None
     if not args.no_e2e:
@@ -1005,7 +1013,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "V": V, "E": g.E,
+        "config": {"workload": workload_label(args), "desc": desc, "V": V, "E": g.E,
                    "queries_per_step": len(srcs), "tune": tune_desc,
                    "l2": "flushed before each query (256 MiB write, untimed)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
