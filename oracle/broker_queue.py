@@ -33,6 +33,11 @@ Two things live here, both written from Sec. III-A and Algorithm 1:
     single-shot split counters) as step generators, for the same seeded
     interleavings.
 
+``CtaRingSim``
+    The single-CTA path's shared-memory ring (take and fill tickets, slots
+    filled by compare-and-swap from empty and taken by exchange) as step
+    generators.
+
 ``check_fifo_positions``
     The property the GPU queue kernels are checked against: an item dequeued
     at ticket position p is exactly the item enqueued at position p, positions
@@ -289,6 +294,78 @@ class WarpQueueSim:
         if self.form == "split":
             self._fetch_add("free", got)
             yield "step"
+        return out
+
+
+class CtaRingSim:
+    """The vertex ring of the single-CTA path (one CTA, shared memory) as
+    step generators: a take ticket (head) and a fill ticket (tail) over C
+    slots; a warp reserves up to k items with one compare-and-swap on head
+    (the warp-aggregated ensure of Algorithm 1, at CTA scope), a filler takes
+    its tickets with one fetch-add on tail; a slot is filled by compare-and-
+    swap from empty and taken by exchange with empty.  Two tickets a lap
+    apart that meet on one slot may swap items, but no item is taken twice
+    or lost.  The caller keeps at most C items filled-or-reserved and not
+    yet taken (in the kernel the in-queue flag does: a vertex is queued at
+    most once, and C >= V), so a filler only ever waits for a taker that has
+    already reserved the item in its slot."""
+
+    def __init__(self, capacity: int):
+        self.C = capacity
+        self.head = 0
+        self.tail = 0
+        self.slots = [None] * capacity
+        self.fill_ticket = {}        # item -> ticket it was filled at
+        self.take_ticket = {}        # item -> ticket it was taken at
+
+    def fill(self, items):
+        """Generator: publish items; returns their first ticket."""
+        p = self.tail                # fetch-add on the fill ticket
+        self.tail += len(items)
+        yield "step"
+        for i, x in enumerate(items):
+            s = (p + i) % self.C
+            while self.slots[s] is not None:       # compare-and-swap fails: full
+                yield "wait"
+            self.slots[s] = x                      # compare-and-swap succeeds
+            self.fill_ticket[x] = p + i
+            yield "step"
+        return p
+
+    def take(self, kmax: int, racy: bool = False):
+        """Generator: take up to kmax items; returns them ([] if none).
+        racy=True reads a slot and empties it in two steps instead of one
+        exchange (kept to show that two takers meeting on a slot can then
+        both take its item)."""
+        h = self.head
+        yield "step"
+        while True:
+            avail = self.tail - h
+            if avail <= 0:
+                return []
+            k = min(avail, kmax)
+            if self.head == h:                     # compare-and-swap on head
+                self.head = h + k
+                yield "step"
+                break
+            h = self.head
+            yield "step"
+        out = []
+        for i in range(k):
+            s = (h + i) % self.C
+            while True:
+                if racy:
+                    x = self.slots[s]
+                    yield "step"
+                    self.slots[s] = None
+                else:
+                    x, self.slots[s] = self.slots[s], None     # exchange with empty
+                if x is not None:
+                    self.take_ticket[x] = h + i
+                    out.append(x)
+                    yield "step"
+                    break
+                yield "wait"
         return out
 
 
