@@ -672,8 +672,13 @@ def small_graph_leg(dev, g, name, reps=3, rounds=True):
         t = bfq.bfq_autotune(h, srcs)
         out["tune"] = {"share_div": t.share_div, "chunk_batch": t.chunk_batch,
                        "batch_items": t.batch_items, "kernel_ctas": t.kernel_ctas,
-                       "queue_form": t.queue_form, "l2_persist_pct": t.l2_persist_pct}
+                       "queue_form": t.queue_form, "l2_persist_pct": t.l2_persist_pct,
+                       "relax_atomic": t.relax_atomic, "small_path": t.small_path,
+                       "small_threads": t.small_threads}
         out["autotuned"] = per_query()
+        st = bfq.bfq_get_stats(h)                # the tuned path, as the last query ran
+        out["path"] = ("single CTA" if st["grid"] == 1 else "persistent") + \
+            f" ({st['grid']} x {st['block']} threads)"
         if rounds:
             try:
                 out["rounds"] = rounds_leg(h, srcs, dist, flush, stream,
@@ -837,7 +842,10 @@ def run_ours(args):
                  "batch_items": tuned.batch_items,
                  "kernel_ctas": tuned.kernel_ctas or ("3 (auto)" if g.E < 8 * V else "4 (auto)"),
                  "queue_form": {0: "exact (auto)", 1: "exact", 2: "single_shot"}[tuned.queue_form],
-                 "l2_persist_pct": tuned.l2_persist_pct}
+                 "l2_persist_pct": tuned.l2_persist_pct,
+                 "relax_atomic": {0: "auto", 1: "atomic_min", 2: "cas",
+                                  3: "filtered"}[tuned.relax_atomic],
+                 "small_path": {0: "auto", 1: "on", 2: "off"}[tuned.small_path]}
 
     def one_step(record):
         """4 queries; returns per-query (device ms, stats)."""

@@ -160,6 +160,11 @@ typedef struct bfq_tune {
                                AUTO takes it for graphs of at most 32,768
                                edges (that fit).
                                Results are the same either way.             */
+  int32_t small_threads;    /* threads of that CTA: 1024 (0 = default) or 512
+                               (fewer warps contending for the queue ring:
+                               faster on deep, narrow searches such as grids,
+                               slower on denser graphs); bfq_autotune tries
+                               both.                                        */
 } bfq_tune;
 
 /* What a single query (bfq_sssp, bfq_sssp_async) does once it has proved a

@@ -39,7 +39,7 @@ class Tune(ctypes.Structure):
                 ("neg_cycle_mode", ctypes.c_int32), ("cycle_walk_hops", ctypes.c_int32),
                 ("relax_atomic", ctypes.c_int32), ("batch_budget_klabels", ctypes.c_int32),
                 ("kernel_ctas", ctypes.c_int32), ("queue_form", ctypes.c_int32),
-                ("small_path", ctypes.c_int32)]
+                ("small_path", ctypes.c_int32), ("small_threads", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

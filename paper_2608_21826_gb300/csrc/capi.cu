@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "bfq_internal.h"
+#include "sssp_small.h"
 
 namespace bfq {
 
@@ -166,6 +167,7 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
   out->kernel_ctas = in->kernel_ctas;
   out->queue_form = in->queue_form;
   out->small_path = in->small_path;
+  out->small_threads = in->small_threads;
   if (out->threads_per_cta != 256)
     return invalid("bfq_tune: threads_per_cta must be 256 (the shared-memory layout of the kernels)");
   if (out->queues_per_cta < 1 || out->queues_per_cta > 8)
@@ -184,7 +186,8 @@ static int fill_tune(const bfq_tune* in, bfq_tune* out) {
       out->relax_atomic < BFQ_RELAX_AUTO || out->relax_atomic > BFQ_RELAX_FILTERED ||
       (out->kernel_ctas != 0 && out->kernel_ctas != 3 && out->kernel_ctas != 4) ||
       out->queue_form < BFQ_QUEUE_FORM_AUTO || out->queue_form > BFQ_QUEUE_FORM_SINGLE_SHOT ||
-      out->small_path < BFQ_SMALL_PATH_AUTO || out->small_path > BFQ_SMALL_PATH_OFF)
+      out->small_path < BFQ_SMALL_PATH_AUTO || out->small_path > BFQ_SMALL_PATH_OFF ||
+      (out->small_threads != 0 && out->small_threads != 512 && out->small_threads != 1024))
     return invalid("bfq_tune: bad limits");
   return BFQ_OK;
 }
@@ -477,9 +480,11 @@ int bfq_sssp_async(bfq_graph_t g, int32_t src, int32_t* dist, int32_t* hops, int
   g->last_stream = s;
   if (use_small_path(g, g->tune)) {
     SsspArgs a = make_args(g, src, dist, hops, pred);
-    g->last_shape = LaunchShape{1, 1024};
+    const int threads = g->tune.small_threads == 512 ? 512 : 1024;
+    g->last_shape = LaunchShape{1, threads};
     g->last_queues = 1;
-    BFQ_CUDA_TRY(launch_sssp_small(a, small_cap_log2(g->V), status_dev, g->ev0, g->ev1, s));
+    BFQ_CUDA_TRY(launch_sssp_small_threads(a, small_cap_log2(g->V), threads, status_dev, g->ev0,
+                                           g->ev1, s));
     if (pred) BFQ_CUDA_TRY(launch_sssp_pred(a, s));
     return BFQ_OK;
   }
@@ -701,10 +706,17 @@ int bfq_autotune(bfq_graph_t g, const int32_t* srcs, int32_t n, bfq_tune* out, v
     }
     if (small_path_fits(g, best_t)) {
       // the other path: one CTA with the search state in shared memory, or
-      // the persistent kernel
-      bfq_tune c = best_t;
-      c.small_path = use_small_path(g, best_t) ? BFQ_SMALL_PATH_OFF : BFQ_SMALL_PATH_ON;
-      try_one(c);
+      // the persistent kernel; then the single CTA's other size
+      {
+        bfq_tune c = best_t;
+        c.small_path = use_small_path(g, best_t) ? BFQ_SMALL_PATH_OFF : BFQ_SMALL_PATH_ON;
+        try_one(c);
+      }
+      if (use_small_path(g, best_t)) {
+        bfq_tune c = best_t;
+        c.small_threads = best_t.small_threads == 512 ? 1024 : 512;
+        try_one(c);
+      }
     }
   }
   cudaStreamSynchronize(s);

@@ -14,12 +14,11 @@
 // walks of the recorded edges.
 #include "bfq_internal.h"
 #include "sssp_common.cuh"
+#include "sssp_small.h"
 
 namespace bfq {
 namespace {
 
-constexpr int kSmallBlock = 1024;
-constexpr int kSmallWarps = kSmallBlock / 32;
 constexpr int kSmallChildBuf = 128;           // claimed children buffered per warp
 constexpr unsigned kEmptySlot = 0xffffffffu;
 
@@ -205,10 +204,15 @@ __device__ __forceinline__ bool small_relax(const SsspArgs& a, long long* lab, l
   return true;
 }
 
-// One CTA of 1024 threads runs the whole query; dynamic shared memory holds
-// labels[V], recorded edges[V] and the ring (2^cap_log2 >= V slots).  On
-// exit the labels are written to a.label, for the epilogue and pred kernels.
-__global__ void __launch_bounds__(kSmallBlock, 1) sssp_small_kernel(SsspArgs a, int cap_log2) {
+// One CTA of BLOCK threads (1024, or 512: fewer warps contend for the ring
+// on deep, narrow searches) runs the whole query; dynamic shared memory
+// holds labels[V], recorded edges[V] and the ring (2^cap_log2 >= V slots).
+// On exit the labels are written to a.label, for the epilogue and pred
+// kernels.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) sssp_small_kernel(SsspArgs a, int cap_log2) {
+  constexpr int kSmallBlock = BLOCK;
+  constexpr int kSmallWarps = BLOCK / 32;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   long long* lab = reinterpret_cast<long long*>(s_dyn);
   long long* cyc = lab + a.V;
@@ -403,34 +407,50 @@ size_t sssp_small_smem(int V, int cap_log2) {
 }
 
 // Largest dynamic shared memory the small kernel can use on the current
-// device (0 when the attribute cannot be set).
-size_t sssp_small_smem_limit() {
-  int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return 0;
+// device, the least over its two block sizes (0 when the attribute cannot
+// be set).
+template <int BLOCK>
+static size_t small_smem_limit_of(int optin) {
   cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, sssp_small_kernel) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, sssp_small_kernel<BLOCK>) != cudaSuccess) return 0;
   if ((size_t)optin <= fa.sharedSizeBytes) return 0;
   const size_t dyn = (size_t)optin - fa.sharedSizeBytes;
-  if (cudaFuncSetAttribute(sssp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn) != cudaSuccess) {
+  if (cudaFuncSetAttribute(sssp_small_kernel<BLOCK>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return dyn;
 }
 
-cudaError_t launch_sssp_small(const SsspArgs& a, int cap_log2, int32_t* status_dev,
-                              cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+size_t sssp_small_smem_limit() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return std::min(small_smem_limit_of<1024>(optin), small_smem_limit_of<512>(optin));
+}
+
+cudaError_t launch_sssp_small_threads(const SsspArgs& a, int cap_log2, int threads,
+                                      int32_t* status_dev, cudaEvent_t ev0, cudaEvent_t ev1,
+                                      cudaStream_t s) {
   if (ev0) cudaEventRecord(ev0, s);
-  sssp_small_kernel<<<1, kSmallBlock, sssp_small_smem(a.V, cap_log2), s>>>(a, cap_log2);
+  const size_t smem = sssp_small_smem(a.V, cap_log2);
+  if (threads == 512)
+    sssp_small_kernel<512><<<1, 512, smem, s>>>(a, cap_log2);
+  else
+    sssp_small_kernel<1024><<<1, 1024, smem, s>>>(a, cap_log2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, s);
   return launch_sssp_epilogue(a, LaunchShape{(a.V + 255) / 256 < 1024 ? (a.V + 255) / 256 : 1024,
                                              256},
                               status_dev, nullptr, s);
+}
+
+cudaError_t launch_sssp_small(const SsspArgs& a, int cap_log2, int32_t* status_dev,
+                              cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+  return launch_sssp_small_threads(a, cap_log2, 1024, status_dev, ev0, ev1, s);
 }
 
 }  // namespace bfq

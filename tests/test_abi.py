@@ -83,7 +83,7 @@ def test_tune_struct_layout_matches_the_header():
     assert t.kernel_ctas == 0
 
 
-@pytest.mark.parametrize("field,value", [("relax_atomic", 4), ("relax_atomic", -1), ("neg_cycle_mode", 2),
+@pytest.mark.parametrize("field,value", [("relax_atomic", 4), ("relax_atomic", -1), ("neg_cycle_mode", 2), ("small_path", 3), ("small_threads", 256),
                                          ("cycle_walk_hops", 1), ("l2_persist_pct", 101),
                                          ("kernel_ctas", 2), ("kernel_ctas", 5)])
 def test_bad_tunes_rejected_before_any_device_work(field, value):

@@ -30,7 +30,7 @@ def _compare(g, src, res, check_pred=False):
 
 def _on_small_path(h):
     s = bfq.bfq_get_stats(h)
-    return s["grid"] == 1 and s["block"] == 1024
+    return s["grid"] == 1 and s["block"] in (512, 1024)
 
 
 def _run_small(g, src, tune=ON, want_pred=True):
@@ -53,13 +53,17 @@ def test_golden(path):
         assert oracle.check_pred(g.row_ptr, g.col, g.w, 0, d, p)
 
 
+ON512 = bfq.make_tune(small_path=bfq.SMALL_PATH_ON, small_threads=512)
+
+
+@pytest.mark.parametrize("tune", [ON, ON512], ids=["1024", "512"])
 @pytest.mark.parametrize("seed", range(24))
-def test_random_with_cycles(seed):
+def test_random_with_cycles(seed, tune):
     rng = np.random.default_rng(700 + seed)
     V = int(rng.integers(1, 8000))
     E = int(rng.integers(0, 12 * V + 1))
     g = synth.random_graph(V, E, seed=1700 + seed, wlo=-3, whi=40)
-    _compare(g, 0, _run_small(g, 0), check_pred=True)
+    _compare(g, 0, _run_small(g, 0, tune), check_pred=True)
 
 
 @pytest.mark.parametrize("seed", range(8))
@@ -70,11 +74,12 @@ def test_random_potential(seed):
     _compare(g, 0, _run_small(g, 0), check_pred=True)
 
 
-def test_grid4k_all_sources_and_auto():
+@pytest.mark.parametrize("tune", [None, ON512], ids=["auto", "512"])
+def test_grid4k_all_sources_and_auto(tune):
     """The 64x64 grid (the default path for it) from every source of the
     workload, against the oracle."""
     g = synth.workload_grid4k()
-    h = gpu_util.create(g)
+    h = gpu_util.create(g, tune)
     try:
         for s in g.sources:
             _compare(g, int(s), gpu_util.run(h, g.V, int(s), want_pred=True), check_pred=True)
@@ -83,9 +88,10 @@ def test_grid4k_all_sources_and_auto():
         bfq.bfq_graph_destroy(h)
 
 
-def test_planted_cycle_found_fast():
+@pytest.mark.parametrize("tune", [ON, ON512], ids=["1024", "512"])
+def test_planted_cycle_found_fast(tune):
     g = synth.plant_negative_cycle(synth.grid_graph(60, 60, seed=3), 5, seed=4)
-    h = gpu_util.create(g, ON)
+    h = gpu_util.create(g, tune)
     try:
         st, _, _, _ = gpu_util.run(h, g.V, 0)
         assert st == bfq.NEG_CYCLE
