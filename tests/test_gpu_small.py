@@ -217,3 +217,27 @@ def test_autotune_tries_both_paths():
         _compare(g, int(g.sources[0]), gpu_util.run(h, g.V, int(g.sources[0])))
     finally:
         bfq.bfq_graph_destroy(h)
+
+
+def test_async_queries_back_to_back_on_one_stream():
+    """Queries enqueued with bfq_sssp_async one after another on a stream
+    (each into its own buffers, statuses on the device), on both block
+    sizes: every result matches the oracle."""
+    import torch
+    g = synth.grid_graph(50, 50, seed=9)
+    srcs = [0, 17, 1234, 2499, 600, 901]
+    for tune in (ON, ON512):
+        h = gpu_util.create(g, tune)
+        try:
+            s = torch.cuda.Stream()
+            dist = [torch.full((g.V,), -7, dtype=torch.int32, device="cuda") for _ in srcs]
+            hops = [torch.full((g.V,), -7, dtype=torch.int32, device="cuda") for _ in srcs]
+            st = torch.full((len(srcs),), -99, dtype=torch.int32, device="cuda")
+            for i, src in enumerate(srcs):
+                bfq.bfq_sssp_async(h, src, dist[i], hops[i], None, st[i:i + 1], s)
+            s.synchronize()
+            assert _on_small_path(h)
+            for i, src in enumerate(srcs):
+                _compare(g, src, (int(st[i]), dist[i].cpu().numpy(), hops[i].cpu().numpy(), None))
+        finally:
+            bfq.bfq_graph_destroy(h)
